@@ -1,0 +1,377 @@
+"""Benchmark of the OS-TV MVCT reconstruction on GB300.
+
+Workload (default): plain OS-TV reconstruction of one 512x512 slice over a
+40 cm FOV from 800 views x 738 equiangular channels (fan beam, SAD 85 cm),
+20 ordered subsets, 500 sub-iterations, TV beta = 1e-3, eps = 1e-6, I0 = 5e3
+Poisson data on a seeded ellipse phantom with low-contrast inserts and rods.
+One step = one full reconstruction (set-up + 500 sub-iterations) of one slice
+per GPU through the C ABI. Metric: slices/s (whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 it is launched by torchrun, one process per GPU; each rank
+reconstructs its own slice (weak scaling, no data-path collective); the time is
+the maximum over ranks. ``--impl reference`` times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1903_10088_gb300 import phantom as ph  # noqa: E402
+
+WORKLOAD = dict(workload="plain OS-TV, one 512^2 slice per step", n=512, fov_cm=40.0, n_views=800,
+                n_channels=738, sad_cm=85.0, subsets=20, sub_iterations=500, beta=1e-3, tv_eps=1e-6,
+                I0=5e3, phantom="water disk + 7 low-contrast inserts + 4 rods (seeded)")
+METRIC = "512^2 slices/s at 500 OS-TV iters (plain); GRay/s; %HBM"
+SEED0 = 100
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+# --------------------------------------------------------------------------
+# accounting
+# --------------------------------------------------------------------------
+def tap_counts(geom: ph.Geometry, n_subsets: int) -> np.ndarray:
+    """In-image Joseph taps (ray, pixel pairs) of every subset: the number of
+    interpolation taps the reprojection reads, equal to the number of
+    residual reads of the matched backprojection. Pure geometry accounting."""
+    n, d = geom.n, geom.delta
+    sx, sy, dx, dy = ph.rays(geom)
+    pc = (n - 1) / 2.0
+    p = np.arange(n, dtype=np.float64) - pc
+    counts = np.zeros(n_subsets, dtype=np.int64)
+    for v in range(geom.n_views):
+        xd = np.abs(dx[v]) >= np.abs(dy[v])
+        m = np.where(xd, dy[v] / np.where(xd, dx[v], 1), dx[v] / np.where(xd, 1, dy[v]))
+        uc = np.where(xd, (sy[v] - sx[v] * m) / d, (sx[v] - sy[v] * m) / d) + pc
+        u = uc[:, None] + m[:, None] * p[None, :]
+        i0 = np.floor(u)
+        inside = ((i0 >= 0) & (i0 < n)).sum() + ((i0 + 1 >= 0) & (i0 + 1 < n)).sum()
+        counts[v % n_subsets] += int(inside)
+    return counts
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mvct_device.cuh", "mvct_recon.cu"):
+        with open(os.path.join(ROOT, "paper_1903_10088_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic():
+    """DRAM bytes per k_recon launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_recon_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_source_sha256_16") != kernel_source_hash():
+        return None
+    return d.get("dram_bytes_per_launch_full_workload")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (testable on CPU with gloo)
+# --------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def slice_seeds(rank: int, per_rank: int):
+    """Each rank reconstructs its own seeded slices; no data is exchanged."""
+    return [SEED0 + rank * per_rank + k for k in range(per_rank)]
+
+
+def max_over_ranks(value: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+def time_oracle(case, sub_iters: int):
+    """Oracle set-up + `sub_iters` sub-iterations; returns (seconds per slice
+    at the full sub-iteration count, sample description)."""
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.setup(case.geom, case.w, case.beta, case.tv_eps)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.recon(case.geom, case.n_subsets, case.p, case.w, case.beta, 0)
+    t_setup2 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.recon(case.geom, case.n_subsets, case.p, case.w, case.beta, sub_iters)
+    t_run = time.perf_counter() - t0
+    t_iter = max(t_run - t_setup2, 1e-9) / sub_iters
+    t_slice = t_setup + case.n_iter * t_iter
+    sample = (f"FP64 oracle, 1 thread: set-up ({t_setup:.2f} s) + {sub_iters} sub-iterations "
+              f"({t_iter * 1e3:.1f} ms each) of the full-size workload, scaled to "
+              f"{case.n_iter} sub-iterations per slice")
+    return t_slice, sample
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    case = ph.make_case("full", SEED0)
+    steps = []
+    sample = ""
+    for _ in range(args.warmup):
+        time_oracle(case, 2)
+    for _ in range(args.steps):
+        t_slice, sample = time_oracle(case, args.ref_sub_iters)
+        steps.append(t_slice)
+    t = float(np.mean(steps))
+    value = 1.0 / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, l2="n/a (CPU)"),
+        "cpu_baseline": {"value": value, "unit": "slices/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1903_10088_gb300 import mvct
+
+    mvct.lib()
+    cases = [ph.make_case("full", s) for s in slice_seeds(rank, 1)]
+    case = cases[0]
+    g = case.geom
+    plan = mvct.Plan(g, case.n_subsets)
+    p = torch.from_numpy(case.p).to(dev)
+    w = torch.from_numpy(case.w).to(dev)
+    img = torch.empty((g.n, g.n), device=dev, dtype=torch.float32)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return plan.recon(p, w, case.beta, case.n_iter, img=img)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----------------------------------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    loop_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))          # evict L2 between timed steps
+            ev[k][0].record(stream)
+            _, res = step()
+            ev[k][1].record(stream)
+            loop_ms.append(res.loop_ms)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = float(np.sum(step_ms))
+    t_max = max_over_ranks(t_local, dev)
+    slices = ws * args.steps
+    value = slices / (t_max / 1e3)
+
+    # ---- end to end through host buffers -------------------------------
+    hp = torch.from_numpy(case.p).pin_memory()
+    hw = torch.from_numpy(case.w).pin_memory()
+    hout = torch.empty((g.n, g.n), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    barrier()
+    for k in range(max(1, args.steps)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p.copy_(hp, non_blocking=True)
+        w.copy_(hw, non_blocking=True)
+        plan.recon(p, w, case.beta, case.n_iter, img=img)
+        hout.copy_(img, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = max_over_ranks(float(np.sum(e2e_ms)), dev)
+    e2e_value = ws * len(e2e_ms) / (e2e_t / 1e3)
+
+    # ---- roofline of the dominant kernel (the persistent loop) ---------
+    taps = tap_counts(g, case.n_subsets)
+    taps_per_launch = float(sum(taps[n % case.n_subsets] for n in range(case.n_iter)))
+    tap_bytes = 2 * 4 * taps_per_launch  # reprojection taps + matched-adjoint residual reads
+    loop_s = float(np.mean(loop_ms)) / 1e3
+    peaks, peak_kind = load_peaks()
+    achieved = tap_bytes / loop_s / 1e9
+    traffic = ncu_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "kernel": "k_recon (persistent OS-TV loop)",
+                "algorithmic_bytes": "4 B x (Joseph reprojection taps + matched-backprojection residual reads) "
+                                     f"= {tap_bytes:.4g} B per launch",
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+    gray = 2.0 * taps_per_launch / loop_s / 1e9
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_slice, sample = time_oracle(case, args.ref_sub_iters)
+        cpu = {"value": 1.0 / t_slice, "unit": "slices/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    launches_per_step = 3  # k_forward (set-up), k_setup_back, k_recon
+    if case.n_iter % 2:
+        launches_per_step += 0  # the odd-count copy-back is a memcpy, not a kernel
+    line = {
+        "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(WORKLOAD, l2="flushed between timed steps (512 MiB write)",
+                       parallelism=f"replicas x{ws}, one slice per GPU per step"),
+        "gray_per_s": gray, "loop_ms_per_slice": float(np.mean(loop_ms)),
+        "setup_and_loop_ms_per_slice": float(np.mean(step_ms)),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "slices/s",
+                "h2d_bytes_per_step": int(hp.numel() * 4 + hw.numel() * 4),
+                "d2h_bytes_per_step": int(hout.numel() * 4)},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "grid_blocks": res.grid_blocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ref-sub-iters", type=int, default=40,
+                    help="oracle sub-iterations timed per reference sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

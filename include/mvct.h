@@ -1,0 +1,161 @@
+/*
+ * mvct.h -- C ABI of the GB300 (sm_103a) OS-TV statistical iterative MVCT
+ * reconstruction library, libmvct.so.
+ *
+ * Method: Ozaki et al., "Fast Statistical Iterative Reconstruction for MVCT in
+ * TomoTherapy", arXiv:1903.10088. The library runs the ordered-subset gradient
+ * loop of Sec. 2-3 (Eq. 1-5, Sec. 3.3.2, Sec. 3.4) on one GPU: per
+ * sub-iteration it reprojects the current image along the fan-beam rays of one
+ * view subset, forms the weighted residual against the measured log
+ * projections, backprojects it with the matched adjoint, adds the smoothed TV
+ * gradient and steps with the adaptive convergence parameter.
+ *
+ * Conventions shared by every entry point
+ *  - Image: float32, n x n, row-major, row i = y, column j = x; pixel centres
+ *    x_j = (j - (n-1)/2) * delta, y_i = (i - (n-1)/2) * delta, delta = fov/n.
+ *  - Sinogram: float32, view-major [rows][n_channels]. "subset = -1" means all
+ *    views in natural order (rows = n_views); "subset = s" means the thinned
+ *    sinogram of views v = s + k*S, k = 0 .. n_views/S - 1 (Sec. 3.4).
+ *  - View v: source at sad*(cos b, sin b), b = view0 + 2 pi v / n_views.
+ *    Channel c: angle g = (c - (C-1)/2 + channel_offset) * fan / C on an
+ *    equiangular arc; ray direction = Rot(g) (-cos b, -sin b).
+ *  - All d_* pointers are caller-owned DEVICE memory on the plan's device,
+ *    float32 unless stated, contiguous, 4-byte aligned; the library never frees
+ *    them. Host pointers are named without the d_ prefix.
+ *  - stream is a cudaStream_t (NULL = legacy default stream). Calls are
+ *    asynchronous on it except mvct_plan_create and mvct_recon (see below).
+ *    A plan owns scratch buffers: calls on one plan must not overlap in time
+ *    (issue them on one stream or synchronise between streams).
+ *  - Return value: MVCT_OK (0) or a negative MVCT_E* code; the message of the
+ *    last failure on the calling thread is returned by mvct_last_error().
+ *    Arguments are validated before anything is enqueued.
+ */
+#ifndef MVCT_H_
+#define MVCT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MVCT_OK 0
+#define MVCT_EINVAL (-1)   /* invalid argument or geometry */
+#define MVCT_ENOMEM (-2)   /* device or host allocation failed */
+#define MVCT_ECUDA (-3)    /* a CUDA runtime call failed */
+#define MVCT_ELAUNCH (-4)  /* the persistent grid cannot be co-resident */
+#define MVCT_ETIMEOUT (-5) /* a grid barrier of the persistent loop timed out */
+#define MVCT_EDATA (-6)    /* non-finite or negative input data */
+
+#define MVCT_MAX_N 4096        /* largest image side */
+#define MVCT_MAX_SUBSETS 1024  /* largest number of ordered subsets */
+
+/* Scanner and image grid (Sec. 3.1, 3.4). Lengths in cm, angles in rad. */
+typedef struct mvct_geometry {
+    int32_t n;              /* image side, 1 .. MVCT_MAX_N */
+    double fov_cm;          /* field of view; pixel size delta = fov_cm / n */
+    double sad_cm;          /* source-isocentre distance; must exceed fov_cm*sqrt(2)/2 */
+    double sdd_cm;          /* source-detector distance (not used by an arc detector) */
+    int32_t n_views;        /* V >= 1, uniform over 2 pi */
+    int32_t n_channels;     /* C >= 1, equiangular */
+    double view0_rad;       /* angle of view 0 */
+    double fan_angle_rad;   /* <= 0 selects 2 asin((fov/2)/sad) */
+    double channel_offset;  /* detector shift in channels */
+} mvct_geometry;
+
+typedef struct mvct_plan_s *mvct_plan;
+
+/* Loop state carried between calls to resume a reconstruction (host memory).
+ * A run of N sub-iterations resumed after K equals one run of K + N, bit for bit. */
+typedef struct mvct_recon_state {
+    int64_t n_done;       /* sub-iterations already run (0 for a fresh run) */
+    double lambda;        /* lambda of the last sub-iteration */
+    double phi_prev;      /* square difference of the last sub-iteration */
+    double best_pass;     /* smallest pass sum so far (+inf if none) */
+    int64_t best_n;       /* its sub-iteration (-1 if none) */
+    double phi_ring[MVCT_MAX_SUBSETS]; /* last S square differences, slot n mod S */
+} mvct_recon_state;
+
+/* Options of mvct_recon. Fill with mvct_recon_opts_init() first. */
+typedef struct mvct_recon_opts {
+    double lambda0;       /* Eq. 4-5 initial convergence parameter (0.01) */
+    double dlambda_up;    /* Eq. 4 increment when the square difference fell (1e-4) */
+    double dlambda_down;  /* Eq. 5 decrement when it rose (2e-4) */
+    double lambda_min;    /* floor of lambda (1e-4) */
+    double kappa;         /* step tau = kappa * lambda on the preconditioned gradient (100) */
+    double tv_eps;        /* TV smoothing inside the square root (1e-6) */
+    double mu0;           /* homogeneous initial image in 1/cm, Sec. 3.3.2 (0.05) */
+    int32_t init_from_input;       /* 1: start from d_img_inout instead of mu0 */
+    float *d_best_out;             /* device n*n: image at the best pass sum, or NULL */
+    const double *lambda_schedule; /* host, n_iter values replacing Eq. 4-5, or NULL */
+    mvct_recon_state *state;       /* host in/out resume state, or NULL */
+    double barrier_timeout_ms;     /* grid-barrier wait limit (2000) */
+    int32_t debug_unreachable_barrier; /* test knob: the first barrier can never complete */
+} mvct_recon_opts;
+
+/* Results of mvct_recon (host memory; arrays caller-owned, may be NULL). */
+typedef struct mvct_recon_stats {
+    double *phi;          /* n_iter square differences Phi_n (unweighted, subset rays) */
+    double *lambda;       /* n_iter convergence parameters lambda_n */
+    int64_t best_n;       /* sub-iteration of the smallest pass sum (-1 if none) */
+    double best_pass;     /* that pass sum */
+    double loop_ms;       /* device time of the persistent loop kernel */
+    double setup_ms;      /* device time of the set-up kernels */
+    int32_t grid_blocks;  /* persistent grid size used */
+    int32_t block_threads;
+} mvct_recon_stats;
+
+/* Default options (the paper's constants: lambda0 0.01, +1e-4, -2e-4; mu0 0.05). */
+void mvct_recon_opts_init(mvct_recon_opts *opts);
+
+/* Build a plan for geometry *g with n_subsets ordered subsets (Sec. 3.4:
+ * thinning with an equal interval; n_views % n_subsets must be 0). Allocates
+ * the ray and view tables and scratch on the CURRENT device and computes the
+ * support mask (A^T 1 > 0) there; synchronous. *out receives the plan. */
+int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_plan *out);
+
+/* Free a plan and its device memory (NULL is ignored). Synchronises the device. */
+void mvct_plan_destroy(mvct_plan plan);
+
+/* Reprojection (Sec. 4.4): d_sino = A_s d_img, Joseph interpolation along each
+ * fan-beam ray. d_img: n*n; d_sino: rows*C with rows = V (subset -1) or V/S. */
+int mvct_forward(mvct_plan plan, const float *d_img, float *d_sino, int32_t subset, void *stream);
+
+/* Estimation (Sec. 4.4): d_img = A_s^T d_sino, the matched adjoint of
+ * mvct_forward, gathered per pixel without atomics (deterministic).
+ * Overwrites all n*n pixels. */
+int mvct_back(mvct_plan plan, const float *d_sino, float *d_img, int32_t subset, void *stream);
+
+/* Gradient of the smoothed TV regulariser (Sec. 2):
+ * TV_eps = sum sqrt(dx^2 + dy^2 + eps), forward differences, zero across the
+ * last row/column. d_grad: n*n; d_tv_or_null: one double (device) receiving
+ * TV_eps, reduced in FP64 in a fixed order. */
+int mvct_tv_grad(mvct_plan plan, const float *d_img, double eps, float *d_grad,
+                 double *d_tv_or_null, void *stream);
+
+/* Objective Psi = 1/2 sum_i w_i ([A img]_i - p_i)^2 + beta TV_eps(img) over all
+ * views (Eq. 2 in its weighted-least-squares reading), FP64 reduction.
+ * d_sino, d_weights: V*C; d_out: one double (device). */
+int mvct_objective(mvct_plan plan, const float *d_img, const float *d_sino, const float *d_weights,
+                   double beta, double eps, double *d_out, void *stream);
+
+/* The ordered-subset TV reconstruction (Eq. 3-5, Sec. 3.3.2, 3.4, 4.2).
+ * d_sino: measured log projections p [V][C]; d_weights: statistical weights w
+ * [V][C] (>= 0); beta: TV weight; n_iter: sub-iterations (each uses one subset,
+ * s = n mod S). d_img_inout: n*n, in = starting image if opts->init_from_input,
+ * out = final iterate. Runs the set-up kernels and one persistent cooperative
+ * kernel on `stream`, then synchronises it and fills *stats (may be NULL).
+ * Returns MVCT_ETIMEOUT if a grid barrier exceeded opts->barrier_timeout_ms,
+ * MVCT_EDATA on non-finite p/w or negative w, MVCT_ELAUNCH if the grid cannot
+ * be co-resident. */
+int mvct_recon(mvct_plan plan, const float *d_sino, const float *d_weights, double beta,
+               int32_t n_iter, const mvct_recon_opts *opts, float *d_img_inout,
+               mvct_recon_stats *stats, void *stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *mvct_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MVCT_H_ */

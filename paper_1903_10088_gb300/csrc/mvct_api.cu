@@ -1,0 +1,251 @@
+// C-ABI entry points: plan construction, argument validation and the
+// stand-alone operators (mvct_forward, mvct_back, mvct_tv_grad, mvct_objective).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "mvct_plan.h"
+
+using namespace mvct;
+
+static thread_local char g_err[512] = "";
+
+int mvct_fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+extern "C" const char *mvct_last_error(void) { return g_err; }
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = (call);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return mvct_fail(MVCT_ECUDA, "%s: %s", #call, cudaGetErrorString(_e));       \
+    } while (0)
+
+const double kPi = 3.14159265358979323846;
+
+double fan_of(const mvct_geometry &g)
+{
+    return g.fan_angle_rad > 0 ? g.fan_angle_rad : 2.0 * std::asin((g.fov_cm / 2.0) / g.sad_cm);
+}
+
+int validate(const mvct_geometry *g, int S)
+{
+    if (!g) return mvct_fail(MVCT_EINVAL, "geometry is NULL");
+    if (g->n < 1 || g->n > MVCT_MAX_N) return mvct_fail(MVCT_EINVAL, "n = %d outside 1..%d", g->n, MVCT_MAX_N);
+    if (g->n_views < 1 || g->n_channels < 1 || g->n_views > 65536 || g->n_channels > 65536 ||
+        (long long)g->n_views * g->n_channels > (1ll << 28))
+        return mvct_fail(MVCT_EINVAL, "views/channels out of range (%d x %d)", g->n_views, g->n_channels);
+    if (!std::isfinite(g->fov_cm) || !(g->fov_cm > 0)) return mvct_fail(MVCT_EINVAL, "fov_cm must be > 0");
+    if (!std::isfinite(g->sad_cm) || !(g->sad_cm > g->fov_cm * std::sqrt(2.0) / 2.0))
+        return mvct_fail(MVCT_EINVAL, "sad_cm must exceed fov_cm*sqrt(2)/2 (source outside the image)");
+    if (!std::isfinite(g->view0_rad) || !std::isfinite(g->channel_offset) || !std::isfinite(g->fan_angle_rad))
+        return mvct_fail(MVCT_EINVAL, "non-finite geometry field");
+    if (g->fan_angle_rad >= kPi) return mvct_fail(MVCT_EINVAL, "fan_angle_rad must be < pi");
+    if (S < 1 || S > MVCT_MAX_SUBSETS || S > g->n_views || g->n_views % S != 0)
+        return mvct_fail(MVCT_EINVAL, "n_subsets = %d must divide n_views = %d (and be <= %d)", S,
+                         g->n_views, MVCT_MAX_SUBSETS);
+    return MVCT_OK;
+}
+
+// Ray and view tables in FP64, stored as FP32 (layout in mvct_device.cuh).
+void build_tables(const mvct_geometry &g, int S, std::vector<float4> &rays, std::vector<float4> &views,
+                  Geo &geo)
+{
+    const int n = g.n, V = g.n_views, C = g.n_channels;
+    const double delta = g.fov_cm / n, pc = (n - 1) / 2.0;
+    const double dg = fan_of(g) / C;
+    rays.resize((size_t)V * C);
+    views.resize(V);
+    for (int v = 0; v < V; ++v) {
+        const double b = g.view0_rad + 2.0 * kPi * v / V;
+        const double sx = g.sad_cm * std::cos(b), sy = g.sad_cm * std::sin(b);
+        const double ex = -std::cos(b), ey = -std::sin(b);
+        views[v] = make_float4((float)sx, (float)sy, (float)ex, (float)ey);
+        for (int c = 0; c < C; ++c) {
+            const double gm = (c - (C - 1) / 2.0 + g.channel_offset) * dg;
+            const double dx = std::cos(gm) * ex - std::sin(gm) * ey;
+            const double dy = std::sin(gm) * ex + std::cos(gm) * ey;
+            float4 r;
+            if (std::fabs(dx) >= std::fabs(dy)) { // x-driven: walk columns, interpolate rows
+                const double m = dy / dx;
+                r = make_float4((float)((sy - sx * m) / delta + pc), (float)m, (float)(delta / std::fabs(dx)), 1.f);
+            } else {                              // y-driven: walk rows, interpolate columns
+                const double m = dx / dy;
+                r = make_float4((float)((sx - sy * m) / delta + pc), (float)m, (float)(delta / std::fabs(dy)), 0.f);
+            }
+            rays[(size_t)v * C + c] = r;
+        }
+    }
+    geo.n = n;
+    geo.V = V;
+    geo.C = C;
+    geo.S = S;
+    geo.Vs = V / S;
+    geo.pc = (float)pc;
+    geo.delta = (float)delta;
+    geo.inv_dgamma = (float)(1.0 / dg);
+    geo.c_mid = (float)((C - 1) / 2.0 - g.channel_offset);
+}
+
+void free_plan(mvct_plan_s *P)
+{
+    if (!P) return;
+    void *ptrs[] = {P->rays, P->views, P->a1t, P->ones_img, P->imgT, P->sino_tmp, P->mu1, P->muT0,
+                    P->muT1, P->D, P->e, P->partials, P->partials2, P->tv_sum, P->bar,
+                    P->loop_state, P->hist, P->sched};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete P;
+}
+
+int check_plan_subset(mvct_plan P, int subset, const char *who)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "%s: null plan", who);
+    if (subset < -1 || subset >= P->geo.S)
+        return mvct_fail(MVCT_EINVAL, "%s: subset %d outside -1..%d", who, subset, P->geo.S - 1);
+    return MVCT_OK;
+}
+
+} // namespace
+
+extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_plan *out)
+{
+    if (!out) return mvct_fail(MVCT_EINVAL, "mvct_plan_create: out is NULL");
+    *out = nullptr;
+    int rc = validate(g, n_subsets);
+    if (rc) return rc;
+    mvct_plan_s *P = new mvct_plan_s();
+    P->g = *g;
+    CK(cudaGetDevice(&P->device));
+    CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
+
+    std::vector<float4> rays, views;
+    build_tables(*g, n_subsets, rays, views, P->geo);
+    const size_t nn = (size_t)g->n * g->n, R = (size_t)g->n_views * g->n_channels;
+    const size_t Rs = (size_t)P->geo.Vs * g->n_channels;
+    P->reduce_grid = P->num_sms * 8;
+    P->recon_grid = recon_occupancy(P);
+    P->partials_cap = std::max(P->reduce_grid, P->recon_grid);
+
+    bool ok = cudaMalloc(&P->rays, R * sizeof(float4)) == cudaSuccess &&
+              cudaMalloc(&P->views, g->n_views * sizeof(float4)) == cudaSuccess &&
+              cudaMalloc(&P->a1t, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->ones_img, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->imgT, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->sino_tmp, R * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->mu1, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->muT0, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->muT1, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->D, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->e, Rs * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->partials, P->partials_cap * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&P->partials2, P->partials_cap * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&P->tv_sum, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&P->bar, sizeof(Barrier)) == cudaSuccess &&
+              cudaMalloc(&P->loop_state, sizeof(mvct_recon_state)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_plan(P);
+        return mvct_fail(MVCT_ENOMEM, "mvct_plan_create: device allocation failed (n=%d, %d x %d rays)",
+                         g->n, g->n_views, g->n_channels);
+    }
+    cudaStream_t st = 0;
+    cudaError_t e = cudaMemcpy(P->rays, rays.data(), R * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->views, views.data(), g->n_views * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_fill(P->ones_img, nn, 1.f, st);
+    if (e == cudaSuccess) e = launch_fill(P->sino_tmp, R, 1.f, st);
+    if (e == cudaSuccess) e = launch_back(P, P->sino_tmp, P->a1t, -1, st); // A^T 1
+    if (e == cudaSuccess) e = cudaMemset(P->bar, 0, sizeof(Barrier));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        free_plan(P);
+        return mvct_fail(MVCT_ECUDA, "mvct_plan_create: %s", cudaGetErrorString(e));
+    }
+    *out = P;
+    return MVCT_OK;
+}
+
+extern "C" void mvct_plan_destroy(mvct_plan P)
+{
+    if (!P) return;
+    DeviceGuard dg(P->device);
+    cudaDeviceSynchronize();
+    free_plan(P);
+}
+
+extern "C" int mvct_forward(mvct_plan P, const float *d_img, float *d_sino, int32_t subset, void *stream)
+{
+    int rc = check_plan_subset(P, subset, "mvct_forward");
+    if (rc) return rc;
+    if (!d_img || !d_sino) return mvct_fail(MVCT_EINVAL, "mvct_forward: null device pointer");
+    DeviceGuard dg(P->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_transpose(d_img, P->imgT, P->geo.n, st));
+    CK(launch_forward(P, d_img, P->imgT, d_sino, subset, nullptr, nullptr, nullptr, st));
+    return MVCT_OK;
+}
+
+extern "C" int mvct_back(mvct_plan P, const float *d_sino, float *d_img, int32_t subset, void *stream)
+{
+    int rc = check_plan_subset(P, subset, "mvct_back");
+    if (rc) return rc;
+    if (!d_img || !d_sino) return mvct_fail(MVCT_EINVAL, "mvct_back: null device pointer");
+    DeviceGuard dg(P->device);
+    CK(launch_back(P, d_sino, d_img, subset, (cudaStream_t)stream));
+    return MVCT_OK;
+}
+
+extern "C" int mvct_tv_grad(mvct_plan P, const float *d_img, double eps, float *d_grad,
+                            double *d_tv_or_null, void *stream)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: null plan");
+    if (!d_img || !d_grad) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: null device pointer");
+    if (!(eps > 0) || !std::isfinite(eps)) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: eps must be > 0");
+    DeviceGuard dg(P->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_tv(P, d_img, (float)eps, d_grad, P->partials, st));
+    if (d_tv_or_null)
+        CK(launch_final_sum(P->partials, P->reduce_grid, 1.0, nullptr, 0, 0.0, d_tv_or_null, st));
+    return MVCT_OK;
+}
+
+extern "C" int mvct_objective(mvct_plan P, const float *d_img, const float *d_sino, const float *d_weights,
+                              double beta, double eps, double *d_out, void *stream)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "mvct_objective: null plan");
+    if (!d_img || !d_sino || !d_weights || !d_out)
+        return mvct_fail(MVCT_EINVAL, "mvct_objective: null device pointer");
+    if (!(eps > 0) || !std::isfinite(eps) || !std::isfinite(beta))
+        return mvct_fail(MVCT_EINVAL, "mvct_objective: invalid beta/eps");
+    DeviceGuard dg(P->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_transpose(d_img, P->imgT, P->geo.n, st));
+    CK(launch_residual(P, d_img, P->imgT, d_sino, d_weights, P->partials, st));
+    CK(launch_tv(P, d_img, (float)eps, nullptr, P->partials2, st));
+    CK(launch_final_sum(P->partials, P->reduce_grid, 0.5, P->partials2, P->reduce_grid, beta, d_out, st));
+    return MVCT_OK;
+}

@@ -1,0 +1,387 @@
+// The ordered-subset TV loop as one persistent cooperative kernel.
+//
+// Per sub-iteration n (subset s = n mod S; Eq. 3-5, Sec. 3.3.2, 3.4, 4.2):
+//   phase F  one warp per ray of the subset: Joseph reprojection of mu^(n),
+//            residual r = q - p, prescaled weighted residual e = scale*w*r,
+//            FP64 partial sums of r^2 per block
+//   barrier
+//   lambda   every block reduces the partials in the same fixed order, so every
+//            block derives the same Phi_n, lambda_n (Eq. 4-5) and best-iterate
+//            decision without another barrier
+//   phase B  one thread per pixel (warps own 8x4 pixel patches): gathered
+//            matched backprojection of e, TV_eps gradient, surrogate-
+//            preconditioned step, clamp at 0, write mu^(n+1) and its transpose
+//   barrier
+// The image ping-pongs between the caller's buffer and a plan buffer; the
+// transpose copy lets y-driven rays read contiguous memory.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "mvct_plan.h"
+
+namespace mvct {
+
+struct ReconArgs {
+    Geo g;
+    const float4 *rays;
+    const float4 *views;
+    const float *p;
+    const float *w;
+    const float *D;
+    float *mu0, *mu1;   // image ping-pong: sub-iteration it reads mu[it & 1]
+    float *muT0, *muT1; // and their transposes
+    float *e;
+    double *partials;
+    float *best;
+    double *phi_hist;
+    double *lam_hist;
+    const double *sched;
+    mvct_recon_state *st;
+    Barrier *bar;
+    long long n0;
+    int n_iter;
+    double lambda0, dup, ddown, lmin, kappa;
+    float beta, eps;
+    unsigned long long timeout_ns, spin_cap;
+    int debug_unreachable;
+};
+
+__global__ void __launch_bounds__(kThreads) k_recon(ReconArgs a)
+{
+    __shared__ double s_ring[MVCT_MAX_SUBSETS];
+    __shared__ double s_warp[kWarps];
+    __shared__ double s_lambda, s_phi_prev, s_best_pass;
+    __shared__ long long s_best_n;
+    __shared__ float s_tau;
+    __shared__ int s_best_flag;
+
+    const Geo g = a.g;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned int G = gridDim.x;
+    const int gw0 = blockIdx.x * kWarps + warp;
+    const int GW = (int)G * kWarps;
+
+    // Set-up flagged bad input: every block sees the same flag and leaves.
+    if (*(volatile int *)&a.bar->data_err) return;
+
+    for (int k = threadIdx.x; k < g.S; k += kThreads) s_ring[k] = a.st->phi_ring[k];
+    if (threadIdx.x == 0) {
+        s_lambda = a.st->lambda;
+        s_phi_prev = a.st->phi_prev;
+        s_best_pass = a.st->best_pass;
+        s_best_n = a.st->best_n;
+    }
+    __syncthreads();
+
+    const int Rs = g.Vs * g.C;
+    const int ux = (g.n + 7) / 8, uy = (g.n + 3) / 4;
+    const int U = ux * uy;
+    const float S_f = (float)g.S;
+
+    for (int it = 0; it < a.n_iter; ++it) {
+        const long long n = a.n0 + it;
+        const int s = (int)(n % g.S);
+        const bool odd = (it & 1) != 0;
+        const float *cur = odd ? a.mu1 : a.mu0;
+        const float *curT = odd ? a.muT1 : a.muT0;
+        float *nxt = odd ? a.mu0 : a.mu1;
+        float *nxtT = odd ? a.muT0 : a.muT1;
+
+        // ---- phase F: reprojection, residual, square difference -------------
+        double acc = 0.0;
+        for (int ray = gw0; ray < Rs; ray += GW) {
+            const int k = ray / g.C, c = ray - k * g.C;
+            const size_t rv = (size_t)(s + k * g.S) * g.C + c;
+            const float4 r = __ldg(&a.rays[rv]);
+            const float q = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
+            if (lane == 0) {
+                const float res = q - __ldg(a.p + rv);
+                a.e[ray] = r.z * __ldg(a.w + rv) * res;
+                acc += (double)res * (double)res;
+            }
+        }
+        if (lane == 0) s_warp[warp] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kWarps; ++k) t += s_warp[k];
+            a.partials[blockIdx.x] = t;
+        }
+        const unsigned int expect = G + ((it == 0 && a.debug_unreachable) ? 1u : 0u);
+        if (!grid_sync(a.bar, expect, a.timeout_ns, a.spin_cap)) return;
+
+        // ---- adaptive lambda (Eq. 4-5) and best iterate (Sec. 4.2) ----------
+        if (warp == 0) {
+            double t = 0.0;
+            for (unsigned int b = lane; b < G; b += 32) t += a.partials[b];
+            t = warp_sum(t);
+            if (lane == 0) {
+                const double phi = t;
+                double lam;
+                if (a.sched) {
+                    lam = a.sched[it];
+                } else if (n == 0) {
+                    lam = a.lambda0;
+                } else {
+                    lam = s_lambda;
+                    if (phi < s_phi_prev) lam += a.dup;
+                    else if (phi > s_phi_prev) lam -= a.ddown;
+                    if (lam < a.lmin) lam = a.lmin;
+                }
+                s_lambda = lam;
+                s_phi_prev = phi;
+                s_ring[n % g.S] = phi;
+                int bf = 0;
+                if (n >= g.S - 1) {
+                    double pass = 0.0;
+                    for (long long k = n - g.S + 1; k <= n; ++k) pass += s_ring[k % g.S];
+                    if (pass < s_best_pass) {
+                        s_best_pass = pass;
+                        s_best_n = n;
+                        bf = 1;
+                    }
+                }
+                s_best_flag = bf;
+                s_tau = (float)(a.kappa * lam);
+                if (blockIdx.x == 0) {
+                    a.phi_hist[it] = phi;
+                    a.lam_hist[it] = lam;
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- phase B: estimation + TV + preconditioned step -----------------
+        const float tau = s_tau;
+        const bool keep_best = s_best_flag && a.best;
+        for (int u = gw0; u < U; u += GW) {
+            const int py = u / ux, px = u - py * ux;
+            const int i = py * 4 + (lane >> 3), j = px * 8 + (lane & 7);
+            if (i < g.n && j < g.n) {
+                const size_t r = (size_t)i * g.n + j;
+                const float m = cur[r];
+                const float d = __ldg(a.D + r);
+                if (keep_best) a.best[r] = m;
+                float nm = 0.f;
+                if (d > 0.f) {
+                    const float gs = gather_pixel<true, false>(g, a.rays, a.views, a.e, i, j, s, g.Vs);
+                    const float tg = tv_grad_pixel<false>(cur, g.n, i, j, a.eps, nullptr);
+                    nm = fmaxf(0.f, m - tau * d * fmaf(S_f, gs, a.beta * tg));
+                }
+                nxt[r] = nm;
+                nxtT[(size_t)j * g.n + i] = nm;
+            }
+        }
+        if (!grid_sync(a.bar, G, a.timeout_ns, a.spin_cap)) return;
+    }
+
+    if (blockIdx.x == 0) {
+        for (int k = threadIdx.x; k < g.S; k += kThreads) a.st->phi_ring[k] = s_ring[k];
+        if (threadIdx.x == 0) {
+            a.st->n_done = a.n0 + a.n_iter;
+            a.st->lambda = s_lambda;
+            a.st->phi_prev = s_phi_prev;
+            a.st->best_pass = s_best_pass;
+            a.st->best_n = s_best_n;
+        }
+    }
+}
+
+int recon_occupancy(mvct_plan_s *P)
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_recon, kThreads, 0) != cudaSuccess)
+        return 0;
+    return nb * P->num_sms;
+}
+
+} // namespace mvct
+
+using namespace mvct;
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+struct Events {
+    cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+    Events()
+    {
+        for (auto &x : e) cudaEventCreate(&x);
+    }
+    ~Events()
+    {
+        for (auto &x : e)
+            if (x) cudaEventDestroy(x);
+    }
+};
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = (call);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return mvct_fail(MVCT_ECUDA, "%s: %s", #call, cudaGetErrorString(_e));       \
+    } while (0)
+
+} // namespace
+
+extern "C" void mvct_recon_opts_init(mvct_recon_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->lambda0 = 0.01;
+    o->dlambda_up = 1e-4;
+    o->dlambda_down = 2e-4;
+    o->lambda_min = 1e-4;
+    o->kappa = 100.0;
+    o->tv_eps = 1e-6;
+    o->mu0 = 0.05;
+    o->barrier_timeout_ms = 2000.0;
+}
+
+extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weights, double beta,
+                          int32_t n_iter, const mvct_recon_opts *opts_in, float *d_img_inout,
+                          mvct_recon_stats *stats, void *stream)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "mvct_recon: null plan");
+    if (!d_sino || !d_weights || !d_img_inout)
+        return mvct_fail(MVCT_EINVAL, "mvct_recon: null device pointer");
+    if (n_iter < 0) return mvct_fail(MVCT_EINVAL, "mvct_recon: n_iter < 0");
+    if (!std::isfinite(beta) || beta < 0) return mvct_fail(MVCT_EINVAL, "mvct_recon: beta must be finite and >= 0");
+    mvct_recon_opts o;
+    if (opts_in) o = *opts_in;
+    else mvct_recon_opts_init(&o);
+    if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
+        !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0))
+        return mvct_fail(MVCT_EINVAL, "mvct_recon: invalid options");
+    if (o.state && (o.state->n_done < 0 || (o.state->n_done > 0 && !o.init_from_input)))
+        return mvct_fail(MVCT_EINVAL, "mvct_recon: resuming (state->n_done > 0) needs init_from_input = 1");
+    if (P->recon_grid <= 0) return mvct_fail(MVCT_ELAUNCH, "mvct_recon: loop kernel has no occupancy");
+
+    DeviceGuard dg(P->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const Geo &g = P->geo;
+    const size_t nn = (size_t)g.n * g.n;
+
+    if (n_iter > P->hist_cap) {
+        cudaFree(P->hist);
+        cudaFree(P->sched);
+        P->hist = nullptr;
+        P->sched = nullptr;
+        P->hist_cap = 0;
+        if (cudaMalloc(&P->hist, 2 * sizeof(double) * (size_t)n_iter) != cudaSuccess ||
+            cudaMalloc(&P->sched, sizeof(double) * (size_t)n_iter) != cudaSuccess)
+            return mvct_fail(MVCT_ENOMEM, "mvct_recon: cannot allocate %d history entries", n_iter);
+        P->hist_cap = n_iter;
+    }
+
+    mvct_recon_state hs;
+    if (o.state) {
+        hs = *o.state;
+    } else {
+        std::memset(&hs, 0, sizeof(hs));
+        hs.lambda = o.lambda0;
+        hs.best_pass = INFINITY;
+        hs.best_n = -1;
+    }
+    CK(cudaMemcpyAsync(P->loop_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
+    if (o.lambda_schedule && n_iter > 0)
+        CK(cudaMemcpyAsync(P->sched, o.lambda_schedule, sizeof(double) * n_iter, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
+
+    Events ev;
+    CK(cudaEventRecord(ev.e[0], st));
+    // set-up (a0): w .* A1 over all views (and input validation), then D and mu0
+    CK(launch_forward(P, P->ones_img, P->ones_img, P->sino_tmp, -1, d_weights, d_sino,
+                      &P->bar->data_err, st));
+    const double cb = beta * 8.0 / std::sqrt(o.tv_eps);
+    CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0,
+                         d_img_inout, P->muT0, st));
+    CK(cudaEventRecord(ev.e[1], st));
+
+    if (n_iter > 0) {
+        ReconArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.g = g;
+        a.rays = P->rays;
+        a.views = P->views;
+        a.p = d_sino;
+        a.w = d_weights;
+        a.D = P->D;
+        a.mu0 = d_img_inout;
+        a.mu1 = P->mu1;
+        a.muT0 = P->muT0;
+        a.muT1 = P->muT1;
+        a.e = P->e;
+        a.partials = P->partials;
+        a.best = o.d_best_out;
+        a.phi_hist = P->hist;
+        a.lam_hist = P->hist + n_iter;
+        a.sched = o.lambda_schedule ? P->sched : nullptr;
+        a.st = (mvct_recon_state *)P->loop_state;
+        a.bar = P->bar;
+        a.n0 = hs.n_done;
+        a.n_iter = n_iter;
+        a.lambda0 = o.lambda0;
+        a.dup = o.dlambda_up;
+        a.ddown = o.dlambda_down;
+        a.lmin = o.lambda_min;
+        a.kappa = o.kappa;
+        a.beta = (float)beta;
+        a.eps = (float)o.tv_eps;
+        a.timeout_ns = (unsigned long long)(o.barrier_timeout_ms * 1e6);
+        a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
+        a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
+        void *args[] = {&a};
+        cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon, dim3(P->recon_grid),
+                                                     dim3(kThreads), args, 0, st);
+        if (le == cudaErrorCooperativeLaunchTooLarge)
+            return mvct_fail(MVCT_ELAUNCH, "mvct_recon: %d blocks cannot be co-resident", P->recon_grid);
+        if (le != cudaSuccess)
+            return mvct_fail(MVCT_ECUDA, "mvct_recon: cooperative launch: %s", cudaGetErrorString(le));
+        if (n_iter & 1)
+            CK(cudaMemcpyAsync(d_img_inout, P->mu1, nn * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaEventRecord(ev.e[2], st));
+
+    Barrier hb;
+    CK(cudaMemcpyAsync(&hb, P->bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    mvct_recon_state out_state;
+    CK(cudaMemcpyAsync(&out_state, P->loop_state, sizeof(out_state), cudaMemcpyDeviceToHost, st));
+    std::vector<double> hist(2 * (size_t)n_iter);
+    if (n_iter > 0)
+        CK(cudaMemcpyAsync(hist.data(), P->hist, 2 * sizeof(double) * n_iter, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+
+    if (hb.data_err) return mvct_fail(MVCT_EDATA, "mvct_recon: non-finite projections/weights or negative weights");
+    if (hb.err)
+        return mvct_fail(MVCT_ETIMEOUT, "mvct_recon: grid barrier wait exceeded %.1f ms", o.barrier_timeout_ms);
+
+    if (o.state) *o.state = out_state;
+    if (stats) {
+        if (stats->phi && n_iter > 0) std::memcpy(stats->phi, hist.data(), sizeof(double) * n_iter);
+        if (stats->lambda && n_iter > 0) std::memcpy(stats->lambda, hist.data() + n_iter, sizeof(double) * n_iter);
+        stats->best_n = out_state.best_n;
+        stats->best_pass = out_state.best_pass;
+        float t1 = 0.f, t2 = 0.f;
+        cudaEventElapsedTime(&t1, ev.e[0], ev.e[1]);
+        cudaEventElapsedTime(&t2, ev.e[1], ev.e[2]);
+        stats->setup_ms = t1;
+        stats->loop_ms = t2;
+        stats->grid_blocks = P->recon_grid;
+        stats->block_threads = kThreads;
+    }
+    return MVCT_OK;
+}

@@ -1,0 +1,270 @@
+"""Python binding of the C-ABI library ``libmvct.so`` (argument marshalling only).
+
+Every operator runs in the library's CUDA kernels; this module only checks
+tensor shapes/dtypes/devices, passes raw device pointers and the current torch
+CUDA stream through ctypes, and raises on a non-zero return code. There is no
+CPU fallback: if the library is missing, importing this module raises.
+
+Entry points mirror ``include/mvct.h``: :class:`Plan` wraps ``mvct_plan_create``
+/ ``mvct_plan_destroy`` and exposes ``forward``, ``back``, ``tv_grad``,
+``objective`` and ``recon``.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+from .build import LIB as _LIB_PATH
+
+MVCT_MAX_SUBSETS = 1024
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ELAUNCH", -5: "ETIMEOUT", -6: "EDATA"}
+
+
+class MvctError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int32),
+        ("fov_cm", ctypes.c_double),
+        ("sad_cm", ctypes.c_double),
+        ("sdd_cm", ctypes.c_double),
+        ("n_views", ctypes.c_int32),
+        ("n_channels", ctypes.c_int32),
+        ("view0_rad", ctypes.c_double),
+        ("fan_angle_rad", ctypes.c_double),
+        ("channel_offset", ctypes.c_double),
+    ]
+
+
+class ReconState(ctypes.Structure):
+    _fields_ = [
+        ("n_done", ctypes.c_int64),
+        ("lambda_", ctypes.c_double),
+        ("phi_prev", ctypes.c_double),
+        ("best_pass", ctypes.c_double),
+        ("best_n", ctypes.c_int64),
+        ("phi_ring", ctypes.c_double * MVCT_MAX_SUBSETS),
+    ]
+
+
+class ReconOpts(ctypes.Structure):
+    _fields_ = [
+        ("lambda0", ctypes.c_double),
+        ("dlambda_up", ctypes.c_double),
+        ("dlambda_down", ctypes.c_double),
+        ("lambda_min", ctypes.c_double),
+        ("kappa", ctypes.c_double),
+        ("tv_eps", ctypes.c_double),
+        ("mu0", ctypes.c_double),
+        ("init_from_input", ctypes.c_int32),
+        ("d_best_out", ctypes.c_void_p),
+        ("lambda_schedule", ctypes.POINTER(ctypes.c_double)),
+        ("state", ctypes.POINTER(ReconState)),
+        ("barrier_timeout_ms", ctypes.c_double),
+        ("debug_unreachable_barrier", ctypes.c_int32),
+    ]
+
+
+class ReconStats(ctypes.Structure):
+    _fields_ = [
+        ("phi", ctypes.POINTER(ctypes.c_double)),
+        ("lambda_", ctypes.POINTER(ctypes.c_double)),
+        ("best_n", ctypes.c_int64),
+        ("best_pass", ctypes.c_double),
+        ("loop_ms", ctypes.c_double),
+        ("setup_ms", ctypes.c_double),
+        ("grid_blocks", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+    ]
+
+
+EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
+           "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error"]
+
+
+def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"libmvct.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32 = ctypes.c_void_p, ctypes.c_int32
+    lib.mvct_recon_opts_init.argtypes = [ctypes.POINTER(ReconOpts)]
+    lib.mvct_recon_opts_init.restype = None
+    lib.mvct_plan_create.argtypes = [ctypes.POINTER(Geometry), i32, ctypes.POINTER(vp)]
+    lib.mvct_plan_destroy.argtypes = [vp]
+    lib.mvct_plan_destroy.restype = None
+    lib.mvct_forward.argtypes = [vp, vp, vp, i32, vp]
+    lib.mvct_back.argtypes = [vp, vp, vp, i32, vp]
+    lib.mvct_tv_grad.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
+    lib.mvct_objective.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
+    lib.mvct_recon.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(ReconOpts), vp,
+                               ctypes.POINTER(ReconStats), vp]
+    lib.mvct_last_error.restype = ctypes.c_char_p
+    lib.mvct_last_error.argtypes = []
+    return lib
+
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise MvctError(rc, lib().mvct_last_error().decode())
+
+
+def _stream(stream=None) -> int:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def _dev_f32(t: torch.Tensor, numel: int, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32:
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be contiguous with {numel} elements (got {tuple(t.shape)})")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def geometry(g) -> Geometry:
+    """Accepts any object with the geometry fields (e.g. ``phantom.Geometry``)."""
+    return Geometry(g.n, g.fov_cm, g.sad_cm, g.sdd_cm, g.n_views, g.n_channels, g.view0_rad,
+                    g.fan_angle_rad, g.channel_offset)
+
+
+@dataclass
+class ReconResult:
+    phi: np.ndarray
+    lam: np.ndarray
+    best_n: int
+    best_pass: float
+    loop_ms: float
+    setup_ms: float
+    grid_blocks: int
+
+
+class Plan:
+    """A reconstruction plan for one geometry and subset count (``mvct_plan_create``)."""
+
+    def __init__(self, geom, n_subsets: int):
+        self.geom = geom
+        self.n = geom.n
+        self.V, self.C, self.S = geom.n_views, geom.n_channels, n_subsets
+        self._g = geometry(geom)
+        h = ctypes.c_void_p()
+        _check(lib().mvct_plan_create(ctypes.byref(self._g), n_subsets, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mvct_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def rows(self, subset: int) -> int:
+        return self.V if subset < 0 else self.V // self.S
+
+    def forward(self, img: torch.Tensor, subset: int = -1, out: Optional[torch.Tensor] = None,
+                stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.rows(subset), self.C), device=img.device, dtype=torch.float32)
+        _check(lib().mvct_forward(self._h, _dev_f32(img, self.n * self.n, "img"),
+                                  _dev_f32(out, self.rows(subset) * self.C, "out"), subset,
+                                  ctypes.c_void_p(_stream(stream))))
+        return out
+
+    def back(self, sino: torch.Tensor, subset: int = -1, out: Optional[torch.Tensor] = None,
+             stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.n, self.n), device=sino.device, dtype=torch.float32)
+        _check(lib().mvct_back(self._h, _dev_f32(sino, self.rows(subset) * self.C, "sino"),
+                               _dev_f32(out, self.n * self.n, "out"), subset,
+                               ctypes.c_void_p(_stream(stream))))
+        return out
+
+    def tv_grad(self, img: torch.Tensor, eps: float, with_value: bool = True, stream=None):
+        grad = torch.empty((self.n, self.n), device=img.device, dtype=torch.float32)
+        val = torch.zeros(1, device=img.device, dtype=torch.float64) if with_value else None
+        _check(lib().mvct_tv_grad(self._h, _dev_f32(img, self.n * self.n, "img"), eps,
+                                  _dev_f32(grad, self.n * self.n, "grad"),
+                                  ctypes.c_void_p(val.data_ptr()) if val is not None else None,
+                                  ctypes.c_void_p(_stream(stream))))
+        return grad, val
+
+    def objective(self, img, p, w, beta: float, eps: float, stream=None) -> torch.Tensor:
+        out = torch.zeros(1, device=img.device, dtype=torch.float64)
+        R = self.V * self.C
+        _check(lib().mvct_objective(self._h, _dev_f32(img, self.n * self.n, "img"), _dev_f32(p, R, "p"),
+                                    _dev_f32(w, R, "w"), beta, eps, ctypes.c_void_p(out.data_ptr()),
+                                    ctypes.c_void_p(_stream(stream))))
+        return out
+
+    def recon(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter: int,
+              img: Optional[torch.Tensor] = None, init_from_input: bool = False,
+              best_out: Optional[torch.Tensor] = None, lambda_schedule=None,
+              state: Optional[ReconState] = None, stream=None, **opts):
+        """Run ``mvct_recon``; returns (image tensor, ReconResult)."""
+        R = self.V * self.C
+        if img is None:
+            img = torch.zeros((self.n, self.n), device=p.device, dtype=torch.float32)
+        o = ReconOpts()
+        lib().mvct_recon_opts_init(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        o.init_from_input = 1 if init_from_input else 0
+        if best_out is not None:
+            o.d_best_out = ctypes.c_void_p(_dev_f32(best_out, self.n * self.n, "best_out").value)
+        sched = None
+        if lambda_schedule is not None:
+            sched = np.ascontiguousarray(lambda_schedule, dtype=np.float64)
+            if sched.size < n_iter:
+                raise ValueError("lambda_schedule shorter than n_iter")
+            o.lambda_schedule = sched.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if state is not None:
+            o.state = ctypes.pointer(state)
+        phi = np.zeros(max(n_iter, 1))
+        lam = np.zeros(max(n_iter, 1))
+        st = ReconStats()
+        st.phi = phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st.lambda_ = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().mvct_recon(self._h, _dev_f32(p, R, "p"), _dev_f32(w, R, "w"), beta, n_iter,
+                                ctypes.byref(o), _dev_f32(img, self.n * self.n, "img"),
+                                ctypes.byref(st), ctypes.c_void_p(_stream(stream))))
+        return img, ReconResult(phi[:n_iter], lam[:n_iter], st.best_n, st.best_pass, st.loop_ms,
+                                st.setup_ms, st.grid_blocks)
+
+
+def fresh_state() -> ReconState:
+    s = ReconState()
+    s.n_done = 0
+    s.best_pass = math.inf
+    s.best_n = -1
+    return s

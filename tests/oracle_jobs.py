@@ -1,0 +1,16 @@
+"""Oracle runs executed in spawned worker processes by the full-size GPU tests.
+
+Each job regenerates its seeded input (so nothing large is pickled in) and runs
+the FP64 oracle; workers are started with the "spawn" method, never forked
+from a process that already initialised CUDA.
+"""
+import numpy as np
+
+import oracle
+from paper_1903_10088_gb300 import phantom as ph
+
+
+def full_case_recon(seed: int, beta: float, n_iter: int):
+    c = ph.make_case("full", seed, beta=beta, n_iter=n_iter)
+    r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, beta, n_iter)
+    return r["image"].astype(np.float64), r["phi"], r["lam"]
