@@ -49,6 +49,7 @@ extern "C" {
 
 #define MVCT_MAX_N 4096        /* largest image side */
 #define MVCT_MAX_SUBSETS 1024  /* largest number of ordered subsets */
+#define MVCT_NOALLOC_MAX_BLOCKS 2048 /* FP64 slots (16 KiB) of mvct_tv_grad_noalloc's static scratch */
 
 /* Scanner and image grid (Sec. 3.1, 3.4). Lengths in cm, angles in rad. */
 typedef struct mvct_geometry {
@@ -151,6 +152,23 @@ int mvct_objective(mvct_plan plan, const float *d_img, const float *d_sino, cons
 int mvct_recon(mvct_plan plan, const float *d_sino, const float *d_weights, double beta,
                int32_t n_iter, const mvct_recon_opts *opts, float *d_img_inout,
                mvct_recon_stats *stats, void *stream);
+
+/* Allocation-free variant of mvct_tv_grad for callers that may not allocate
+ * device memory (applications that hand out all GPU memory through their own
+ * allocator, or latency-critical paths where cudaMalloc/cudaFree, which can
+ * synchronise the device, are not allowed). The paper has no counterpart; this
+ * is a library-level service. Same operation and outputs as mvct_tv_grad, but
+ * no plan: d_img and d_grad are caller-owned n*n float32 device arrays, n in
+ * 1..MVCT_MAX_N; d_tv_or_null receives TV_eps (one device double) or is NULL.
+ * Allocates nothing: the FP64 partial sums live in a 16 KiB static device array
+ * of the library (MVCT_NOALLOC_MAX_BLOCKS slots) that every GPU loading the
+ * library holds until process exit. The first call on a device, made with that
+ * device current, looks up the array's address there; make that first call
+ * before any stream capture. All calls share the array: calls that overlap on
+ * the GPU (unordered streams) race and corrupt the TV value -- order them.
+ * Returns MVCT_EINVAL for null pointers, n outside 1..MVCT_MAX_N or eps <= 0. */
+int mvct_tv_grad_noalloc(const float *d_img, int32_t n, double eps, float *d_grad,
+                         double *d_tv_or_null, void *stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *mvct_last_error(void);

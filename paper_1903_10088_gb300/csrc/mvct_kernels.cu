@@ -219,6 +219,13 @@ cudaError_t launch_tv(const mvct_plan_s *P, const float *img, float eps, float *
     return cudaGetLastError();
 }
 
+cudaError_t launch_tv_grid(int n, const float *img, float eps, float *grad, double *partials, int grid,
+                           cudaStream_t st)
+{
+    k_tv<<<grid, kThreads, 0, st>>>(n, img, eps, grad, partials);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_final_sum(const double *a, int na, double ca, const double *b, int nb, double cb,
                              double *out, cudaStream_t st)
 {

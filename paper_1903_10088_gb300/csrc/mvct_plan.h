@@ -52,6 +52,8 @@ cudaError_t launch_back(const mvct_plan_s *P, const float *sino, float *img, int
                         cudaStream_t st);
 cudaError_t launch_tv(const mvct_plan_s *P, const float *img, float eps, float *grad,
                       double *partials, cudaStream_t st);
+cudaError_t launch_tv_grid(int n, const float *img, float eps, float *grad, double *partials, int grid,
+                           cudaStream_t st);
 cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float *imgT,
                             const float *p, const float *w, double *partials, cudaStream_t st);
 cudaError_t launch_final_sum(const double *a, int na, double ca, const double *b, int nb, double cb,

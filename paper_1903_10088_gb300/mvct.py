@@ -89,7 +89,8 @@ class ReconStats(ctypes.Structure):
 
 
 EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
-           "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error"]
+           "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error",
+           "mvct_tv_grad_noalloc"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -108,6 +109,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     lib.mvct_objective.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
     lib.mvct_recon.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(ReconOpts), vp,
                                ctypes.POINTER(ReconStats), vp]
+    lib.mvct_tv_grad_noalloc.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp]
     lib.mvct_last_error.restype = ctypes.c_char_p
     lib.mvct_last_error.argtypes = []
     return lib
@@ -260,6 +262,18 @@ class Plan:
                                 ctypes.byref(st), ctypes.c_void_p(_stream(stream))))
         return img, ReconResult(phi[:n_iter], lam[:n_iter], st.best_n, st.best_pass, st.loop_ms,
                                 st.setup_ms, st.grid_blocks)
+
+
+def tv_grad_noalloc(img: torch.Tensor, eps: float, grad: torch.Tensor, tv: Optional[torch.Tensor] = None,
+                    stream=None) -> None:
+    """``mvct_tv_grad_noalloc``: TV gradient (and value) into caller-provided
+    tensors; the library allocates nothing."""
+    n = img.shape[-1]
+    if tv is not None and (not tv.is_cuda or tv.dtype != torch.float64 or tv.numel() < 1):
+        raise TypeError("tv must be a CUDA float64 tensor")
+    _check(lib().mvct_tv_grad_noalloc(_dev_f32(img, n * n, "img"), n, eps, _dev_f32(grad, n * n, "grad"),
+                                      ctypes.c_void_p(tv.data_ptr()) if tv is not None else None,
+                                      ctypes.c_void_p(_stream(stream))))
 
 
 def fresh_state() -> ReconState:
