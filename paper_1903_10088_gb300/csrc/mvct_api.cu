@@ -115,8 +115,8 @@ void free_plan(mvct_plan_s *P)
 {
     if (!P) return;
     void *ptrs[] = {P->rays, P->views, P->a1t, P->ones_img, P->imgT, P->sino_tmp, P->mu1, P->muT0,
-                    P->muT1, P->D, P->e, P->partials, P->partials2, P->tv_sum, P->bar,
-                    P->loop_state, P->hist, P->sched};
+                    P->muT1, P->D, P->e4, P->tile_part, P->tile_flag, P->partials, P->partials2,
+                    P->tv_sum, P->bar, P->loop_state, P->hist, P->sched};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -150,6 +150,13 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     P->reduce_grid = P->num_sms * 8;
     P->recon_grid = recon_occupancy(P);
     P->partials_cap = std::max(P->reduce_grid, P->recon_grid);
+    // phase B of the loop: 32x32 tiles, views split into `groups` blocks per tile
+    // so that tiles x groups fills the co-resident grid
+    P->tiles_x = (g->n + kTile - 1) / kTile;
+    P->n_tiles = P->tiles_x * P->tiles_x;
+    P->groups = std::max(1, std::min(std::min(8, P->geo.Vs), P->recon_grid / P->n_tiles));
+    const size_t part_floats = (size_t)P->n_tiles * (P->groups - 1) * kTile * kTile;
+    const size_t n_flags = (size_t)P->n_tiles * (P->groups - 1);
 
     bool ok = cudaMalloc(&P->rays, R * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->views, g->n_views * sizeof(float4)) == cudaSuccess &&
@@ -161,7 +168,9 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
               cudaMalloc(&P->muT0, nn * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->muT1, nn * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->D, nn * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&P->e, Rs * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->e4, Rs * sizeof(float4)) == cudaSuccess &&
+              (part_floats == 0 || cudaMalloc(&P->tile_part, part_floats * sizeof(float)) == cudaSuccess) &&
+              (n_flags == 0 || cudaMalloc(&P->tile_flag, n_flags * sizeof(unsigned int)) == cudaSuccess) &&
               cudaMalloc(&P->partials, P->partials_cap * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&P->partials2, P->partials_cap * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&P->tv_sum, sizeof(double)) == cudaSuccess &&

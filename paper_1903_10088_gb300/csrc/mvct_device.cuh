@@ -138,6 +138,96 @@ __device__ __forceinline__ float gather_pixel(const Geo &g, const float4 *__rest
     return acc;
 }
 
+// ---------------------------------------------------------------------------
+// Tile splat: the matched backprojection of one subset onto a 32x32 pixel tile.
+//
+// For a view, every ray that can reach the tile is walked across the tile's 32
+// columns (x-driven ray: lane = column, taps at rows i0 and i0+1) or 32 rows
+// (y-driven ray: lane = row, taps at columns j0 and j0+1), with exactly the
+// projector's weights: u = fmaf(m, p - pc, u_c), (1-f) to tap i0 and f to tap
+// i0+1, times the ray's prescaled residual. Each lane only touches its own
+// column (or row) of a warp-private accumulator tile, in channel order, so the
+// result is deterministic without atomics.
+//
+// Accumulator layout: 32 rows x 33 floats. Rays whose slope (dy/dx for x-driven,
+// dx/dy for y-driven) is >= 0 use column index j, rays with negative slopes use
+// the mirrored column 31 - j; either way the 32 lanes of a step fall in at least
+// 16 distinct banks.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 32;
+constexpr int kAccStride = 33;
+constexpr int kAccFloats = kTile * kAccStride;
+
+// Channel window [x, y] of the rays of a view that can carry a non-zero weight to
+// a pixel of the tile whose first row/column are (i_lo, j_lo): a ray with a
+// non-zero Joseph weight passes within one pixel of that pixel's centre, so it
+// crosses the box of pixel centres grown by one pixel; the window is that box's
+// angular extent seen from the source, widened by one channel. Whole warp calls.
+__device__ __forceinline__ int2 tile_window(const Geo &g, float4 vw, int i_lo, int j_lo, int lane)
+{
+    const int corner = lane & 3;
+    const float jj = (corner & 1) ? (float)(j_lo + kTile) : (float)(j_lo - 1);
+    const float ii = (corner & 2) ? (float)(i_lo + kTile) : (float)(i_lo - 1);
+    const float px = (jj - g.pc) * g.delta - vw.x, py = (ii - g.pc) * g.delta - vw.y;
+    const float dot = fmaf(px, vw.z, py * vw.w);
+    const float crs = fmaf(vw.z, py, -vw.w * px);
+    float lo, hi;
+    if (dot > 0.f) {
+        lo = hi = fmaf(atanf(__fdividef(crs, dot)), g.inv_dgamma, g.c_mid);
+    } else { // source inside the grown box (extreme geometry): every channel
+        lo = -INFINITY;
+        hi = INFINITY;
+    }
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int c0 = max(0, (int)floorf(fmaxf(lo, -2.f)) - 1);
+    const int c1 = min(g.C - 1, (int)ceilf(fminf(hi, (float)g.C + 1.f)) + 1);
+    return make_int2(c0, c1);
+}
+
+// Splat channels [c0, c1] of one view onto the warp's accumulator tile.
+// e4row[c] = (u_c, m, prescaled residual, x-driven flag) of the view's rays.
+// pj = j_lo + lane - pc, pi = i_lo + lane - pc. RO: e4row may use the
+// read-only cache (not when it was written earlier in the same kernel).
+template <bool MIRROR, bool RO>
+__device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const float4 *e4row, int c0,
+                                               int c1, float pj, float pi, int i_lo, int j_lo, int lane)
+{
+    for (int cb = c0; cb <= c1; cb += 32) {
+        const int c = cb + lane;
+        if (c <= c1) {
+            if constexpr (RO) stage[lane] = __ldg(e4row + c);
+            else stage[lane] = e4row[c];
+        }
+        __syncwarp();
+        const int cnt = min(32, c1 - cb + 1);
+        for (int t = 0; t < cnt; ++t) {
+            const float4 r = stage[t];
+            if (r.w > 0.5f) { // x-driven: this lane's column, rows a and a+1
+                const float u = fmaf(r.y, pj, r.x);
+                const float fl = floorf(u);
+                const int a = (int)fl - i_lo;
+                const float w1 = (u - fl) * r.z, w0 = r.z - w1;
+                const int col = MIRROR ? (kTile - 1) - lane : lane;
+                if ((unsigned)a < (unsigned)kTile) acc[a * kAccStride + col] += w0;
+                if ((unsigned)(a + 1) < (unsigned)kTile) acc[(a + 1) * kAccStride + col] += w1;
+            } else {          // y-driven: this lane's row, columns a and a+1
+                const float u = fmaf(r.y, pi, r.x);
+                const float fl = floorf(u);
+                const int a = (int)fl - j_lo;
+                const float w1 = (u - fl) * r.z, w0 = r.z - w1;
+                float *row = acc + lane * kAccStride;
+                if ((unsigned)a < (unsigned)kTile) row[MIRROR ? (kTile - 1) - a : a] += w0;
+                if ((unsigned)(a + 1) < (unsigned)kTile) row[MIRROR ? (kTile - 2) - a : a + 1] += w1;
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // d/dmu[i][j] of TV_eps = sum sqrt(dx^2 + dy^2 + eps) with forward differences
 // and zero differences across the last column / row. If phi is non-null it
 // receives sqrt(dx^2 + dy^2 + eps) of the term anchored at (i, j).

@@ -23,7 +23,10 @@ struct mvct_plan_s {
     float *muT0 = nullptr;      // [n*n] transposes of the two loop buffers
     float *muT1 = nullptr;
     float *D = nullptr;         // [n*n] surrogate diagonal (0 off the support)
-    float *e = nullptr;         // [Vs*C] prescaled weighted residual of one subset
+    float4 *e4 = nullptr;       // [Vs*C] (u_c, m, prescaled weighted residual, flag) of one subset
+    float *tile_part = nullptr; // [n_tiles][groups-1][32*32] partial tile backprojections
+    unsigned int *tile_flag = nullptr; // [n_tiles][groups-1] publication stamps
+    int tiles_x = 0, n_tiles = 0, groups = 1; // phase-B decomposition of the loop kernel
     double *partials = nullptr; // [partials_cap] per-block FP64 partial sums
     double *partials2 = nullptr;
     int partials_cap = 0;

@@ -31,8 +31,10 @@ struct ReconArgs {
     const float *D;
     float *mu0, *mu1;   // image ping-pong: sub-iteration it reads mu[it & 1]
     float *muT0, *muT1; // and their transposes
-    float *e;
+    float4 *e4;         // [Vs*C] (u_c, m, prescaled residual, flag) of the subset's rays
     double *partials;
+    float *tile_part;   // [T][H-1][1024] partial backprojections of the non-owner groups
+    unsigned int *tile_flag; // [T][H-1] sub-iteration stamp of each published partial
     float *best;
     double *phi_hist;
     double *lam_hist;
@@ -41,20 +43,42 @@ struct ReconArgs {
     Barrier *bar;
     long long n0;
     int n_iter;
+    int tiles_x, n_tiles, groups; // phase B work: n_tiles x groups items
     double lambda0, dup, ddown, lmin, kappa;
     float beta, eps;
     unsigned long long timeout_ns, spin_cap;
     int debug_unreachable;
 };
 
-__global__ void __launch_bounds__(kThreads) k_recon(ReconArgs a)
+// Wait until flag == stamp (bounded like the grid barrier). Thread 0 only.
+__device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int stamp, Barrier *bar,
+                                          unsigned long long timeout_ns, unsigned long long spin_cap)
+{
+    if (ld_acquire(flag) == stamp) return true;
+    const unsigned long long t0 = global_ns();
+    unsigned long long spins = 0;
+    while (ld_acquire(flag) != stamp) {
+        if (*(volatile int *)&bar->err) return false;
+        ++spins;
+        if (spins > spin_cap || ((spins & 31u) == 0 && global_ns() - t0 > timeout_ns)) {
+            atomicExch(&bar->err, 1);
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
 {
     __shared__ double s_ring[MVCT_MAX_SUBSETS];
     __shared__ double s_warp[kWarps];
     __shared__ double s_lambda, s_phi_prev, s_best_pass;
     __shared__ long long s_best_n;
     __shared__ float s_tau;
-    __shared__ int s_best_flag;
+    __shared__ int s_best_flag, s_ok;
+    __shared__ float s_acc[kWarps][kAccFloats];
+    __shared__ float4 s_stage[kWarps][32];
 
     const Geo g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -75,9 +99,15 @@ __global__ void __launch_bounds__(kThreads) k_recon(ReconArgs a)
     __syncthreads();
 
     const int Rs = g.Vs * g.C;
-    const int ux = (g.n + 7) / 8, uy = (g.n + 3) / 4;
-    const int U = ux * uy;
+    const int H = a.groups;
+    const int n_items = a.n_tiles * H;
+    const int n_nonowner = a.n_tiles * (H - 1);
     const float S_f = (float)g.S;
+    // warps 0..3 take the views whose ray slopes are >= 0, warps 4..7 the others
+    const bool mirror = warp >= kWarps / 2;
+    const int q = warp & (kWarps / 2 - 1);
+    float *acc = s_acc[warp];
+    float4 *stage = s_stage[warp];
 
     for (int it = 0; it < a.n_iter; ++it) {
         const long long n = a.n0 + it;
@@ -87,21 +117,22 @@ __global__ void __launch_bounds__(kThreads) k_recon(ReconArgs a)
         const float *curT = odd ? a.muT1 : a.muT0;
         float *nxt = odd ? a.mu0 : a.mu1;
         float *nxtT = odd ? a.muT0 : a.muT1;
+        const unsigned int stamp = (unsigned int)it + 1u;
 
         // ---- phase F: reprojection, residual, square difference -------------
-        double acc = 0.0;
+        double acc_phi = 0.0;
         for (int ray = gw0; ray < Rs; ray += GW) {
             const int k = ray / g.C, c = ray - k * g.C;
             const size_t rv = (size_t)(s + k * g.S) * g.C + c;
             const float4 r = __ldg(&a.rays[rv]);
-            const float q = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
+            const float q_ray = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
             if (lane == 0) {
-                const float res = q - __ldg(a.p + rv);
-                a.e[ray] = r.z * __ldg(a.w + rv) * res;
-                acc += (double)res * (double)res;
+                const float res = q_ray - __ldg(a.p + rv);
+                a.e4[ray] = make_float4(r.x, r.y, r.z * __ldg(a.w + rv) * res, r.w);
+                acc_phi += (double)res * (double)res;
             }
         }
-        if (lane == 0) s_warp[warp] = acc;
+        if (lane == 0) s_warp[warp] = acc_phi;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
@@ -152,26 +183,112 @@ __global__ void __launch_bounds__(kThreads) k_recon(ReconArgs a)
         }
         __syncthreads();
 
-        // ---- phase B: estimation + TV + preconditioned step -----------------
+        // ---- phase B: tile splat (estimation) + TV + preconditioned step ----
+        // Items: (tile, view group h). Groups h < H-1 publish a partial tile;
+        // group H-1 (the owner) adds the partials in group order and updates
+        // the tile. Non-owner items come first in every block's sequence, so an
+        // owner only ever waits on items that never wait.
         const float tau = s_tau;
         const bool keep_best = s_best_flag && a.best;
-        for (int u = gw0; u < U; u += GW) {
-            const int py = u / ux, px = u - py * ux;
-            const int i = py * 4 + (lane >> 3), j = px * 8 + (lane & 7);
-            if (i < g.n && j < g.n) {
-                const size_t r = (size_t)i * g.n + j;
-                const float m = cur[r];
-                const float d = __ldg(a.D + r);
-                if (keep_best) a.best[r] = m;
-                float nm = 0.f;
-                if (d > 0.f) {
-                    const float gs = gather_pixel<true, false>(g, a.rays, a.views, a.e, i, j, s, g.Vs);
-                    const float tg = tv_grad_pixel<false>(cur, g.n, i, j, a.eps, nullptr);
-                    nm = fmaxf(0.f, m - tau * d * fmaf(S_f, gs, a.beta * tg));
+        for (int item = blockIdx.x; item < n_items; item += G) {
+            const bool owner = item >= n_nonowner;
+            const int t = owner ? item - n_nonowner : item % a.n_tiles;
+            const int h = owner ? H - 1 : item / a.n_tiles;
+            const int i_lo = (t / a.tiles_x) * kTile, j_lo = (t % a.tiles_x) * kTile;
+            const float pj = (float)(j_lo + lane) - g.pc, pi = (float)(i_lo + lane) - g.pc;
+
+            for (int k = lane; k < kAccFloats; k += 32) acc[k] = 0.f;
+            __syncwarp();
+            int cnt = 0;
+            for (int k = h; k < g.Vs; k += H) {
+                const float4 vw = __ldg(&a.views[s + k * g.S]);
+                if ((vw.z * vw.w < 0.f) != mirror) continue; // slope class of the view
+                for (int part = 0; part < 2; ++part, ++cnt) {
+                    if ((cnt & (kWarps / 2 - 1)) != q) continue;
+                    const int2 win = tile_window(g, vw, i_lo, j_lo, lane);
+                    const int mid = (win.x + win.y + 1) >> 1;
+                    const int c0 = part ? mid : win.x, c1 = part ? win.y : mid - 1;
+                    const float4 *row = a.e4 + (size_t)k * g.C;
+                    if (mirror) splat_channels<true, false>(acc, stage, row, c0, c1, pj, pi, i_lo, j_lo, lane);
+                    else splat_channels<false, false>(acc, stage, row, c0, c1, pj, pi, i_lo, j_lo, lane);
                 }
-                nxt[r] = nm;
-                nxtT[(size_t)j * g.n + i] = nm;
             }
+            __syncthreads();
+
+            // sum the warps' tiles in warp order: 4 pixels per thread
+            float part_val[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = threadIdx.x + u * kThreads;
+                const int ii = idx >> 5, jj = idx & 31;
+                float v = 0.f;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w)
+                    v += s_acc[w][ii * kAccStride + (w >= kWarps / 2 ? (kTile - 1) - jj : jj)];
+                part_val[u] = v;
+            }
+
+            if (!owner) {
+                float *dst = a.tile_part + ((size_t)t * (H - 1) + h) * (kTile * kTile);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) __stcg(dst + threadIdx.x + u * kThreads, part_val[u]);
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    __threadfence();
+                    st_release(a.tile_flag + (size_t)t * (H - 1) + h, stamp);
+                }
+                continue;
+            }
+
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                for (int hh = 0; hh < H - 1 && ok; ++hh)
+                    ok = wait_flag(a.tile_flag + (size_t)t * (H - 1) + hh, stamp, a.bar, a.timeout_ns,
+                                   a.spin_cap);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+
+            float *tile = s_acc[0]; // reused for the transposed write-out
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = threadIdx.x + u * kThreads;
+                const int ii = idx >> 5, jj = idx & 31;
+                float gs = 0.f;
+                for (int hh = 0; hh < H - 1; ++hh)
+                    gs += __ldcg(a.tile_part + ((size_t)t * (H - 1) + hh) * (kTile * kTile) + idx);
+                gs += part_val[u];
+                const int i = i_lo + ii, j = j_lo + jj;
+                float nm = 0.f;
+                if (i < g.n && j < g.n) {
+                    const size_t r = (size_t)i * g.n + j;
+                    const float m = cur[r];
+                    const float d = __ldg(a.D + r);
+                    if (keep_best) a.best[r] = m;
+                    if (d > 0.f) {
+                        const float tg = tv_grad_pixel<false>(cur, g.n, i, j, a.eps, nullptr);
+                        nm = fmaxf(0.f, m - tau * d * fmaf(S_f, gs, a.beta * tg));
+                    }
+                    nxt[r] = nm;
+                }
+                part_val[u] = nm;
+            }
+            __syncthreads(); // every warp has finished reading s_acc
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = threadIdx.x + u * kThreads;
+                tile[(idx >> 5) * kAccStride + (idx & 31)] = part_val[u];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int idx = threadIdx.x + u * kThreads;
+                const int jj = idx >> 5, ii = idx & 31; // transposed: row of muT = column j
+                const int i = i_lo + ii, j = j_lo + jj;
+                if (i < g.n && j < g.n) nxtT[(size_t)j * g.n + i] = tile[ii * kAccStride + jj];
+            }
+            __syncthreads(); // tile (s_acc[0]) is zeroed by the next item
         }
         if (!grid_sync(a.bar, G, a.timeout_ns, a.spin_cap)) return;
     }
@@ -300,6 +417,8 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     if (o.lambda_schedule && n_iter > 0)
         CK(cudaMemcpyAsync(P->sched, o.lambda_schedule, sizeof(double) * n_iter, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
+    if (P->tile_flag)
+        CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * (P->groups - 1), st));
 
     Events ev;
     CK(cudaEventRecord(ev.e[0], st));
@@ -324,8 +443,13 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         a.mu1 = P->mu1;
         a.muT0 = P->muT0;
         a.muT1 = P->muT1;
-        a.e = P->e;
+        a.e4 = P->e4;
         a.partials = P->partials;
+        a.tile_part = P->tile_part;
+        a.tile_flag = P->tile_flag;
+        a.tiles_x = P->tiles_x;
+        a.n_tiles = P->n_tiles;
+        a.groups = P->groups;
         a.best = o.d_best_out;
         a.phi_hist = P->hist;
         a.lam_hist = P->hist + n_iter;
