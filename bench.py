@@ -268,7 +268,7 @@ def run_ours(args):
     # ---- device-resident timed region ----------------------------------
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
-    loop_ms = []
+    loop_ms, fwd_ms, back_ms = [], [], []
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
@@ -278,6 +278,8 @@ def run_ours(args):
             _, res = step()
             ev[k][1].record(stream)
             loop_ms.append(res.loop_ms)
+            fwd_ms.append(res.forward_ms)
+            back_ms.append(res.back_ms)
         torch.cuda.synchronize()
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -336,6 +338,8 @@ def run_ours(args):
                        parallelism=f"replicas x{ws}, one slice per GPU per step"),
         "gray_per_s": gray, "loop_ms_per_slice": float(np.mean(loop_ms)),
         "setup_and_loop_ms_per_slice": float(np.mean(step_ms)),
+        "loop_phase_ms_per_slice": {"reprojection+residual": float(np.mean(fwd_ms)),
+                                    "estimation+tv+update": float(np.mean(back_ms))},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "slices/s",

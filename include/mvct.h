@@ -102,6 +102,8 @@ typedef struct mvct_recon_stats {
     double best_pass;     /* that pass sum */
     double loop_ms;       /* device time of the persistent loop kernel */
     double setup_ms;      /* device time of the set-up kernels */
+    double forward_ms;    /* loop time in reprojection + residual (incl. its grid barrier) */
+    double back_ms;       /* loop time in estimation + TV + update (incl. its grid barrier) */
     int32_t grid_blocks;  /* persistent grid size used */
     int32_t block_threads;
 } mvct_recon_stats;

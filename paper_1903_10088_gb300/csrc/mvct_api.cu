@@ -114,9 +114,9 @@ void build_tables(const mvct_geometry &g, int S, std::vector<float4> &rays, std:
 void free_plan(mvct_plan_s *P)
 {
     if (!P) return;
-    void *ptrs[] = {P->rays, P->views, P->a1t, P->ones_img, P->imgT, P->sino_tmp, P->mu1, P->muT0,
-                    P->muT1, P->D, P->e4, P->tile_part, P->tile_flag, P->partials, P->partials2,
-                    P->tv_sum, P->bar, P->loop_state, P->hist, P->sched};
+    void *ptrs[] = {P->rays, P->views, P->a1t, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
+                    P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
+                    P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -150,31 +150,33 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     P->reduce_grid = P->num_sms * 8;
     P->recon_grid = recon_occupancy(P);
     P->partials_cap = std::max(P->reduce_grid, P->recon_grid);
-    // phase B of the loop: 32x32 tiles, views split into `groups` blocks per tile
-    // so that tiles x groups fills the co-resident grid
+    // phase B of the loop: 32x32 tiles, each tile's views dealt round-robin to
+    // `groups` blocks so that tiles x groups fills the grid
     P->tiles_x = (g->n + kTile - 1) / kTile;
     P->n_tiles = P->tiles_x * P->tiles_x;
-    P->groups = std::max(1, std::min(std::min(8, P->geo.Vs), P->recon_grid / P->n_tiles));
-    const size_t part_floats = (size_t)P->n_tiles * (P->groups - 1) * kTile * kTile;
-    const size_t n_flags = (size_t)P->n_tiles * (P->groups - 1);
+    P->groups = std::max(1, std::min(std::min(kMaxGroups, P->geo.Vs), P->recon_grid / P->n_tiles));
+    const size_t part_floats = (size_t)P->n_tiles * P->groups * kTile * kTile;
+    const size_t n_flags = (size_t)P->n_tiles * P->groups;
 
     bool ok = cudaMalloc(&P->rays, R * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->views, g->n_views * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->a1t, nn * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&P->ones_img, nn * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&P->imgT, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->pad[0], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->pad[1], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->pad[2], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->pad[3], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->pad_ones, pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->sino_tmp, R * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&P->mu1, nn * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&P->muT0, nn * sizeof(float)) == cudaSuccess &&
-              cudaMalloc(&P->muT1, nn * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->D, nn * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->e4, Rs * sizeof(float4)) == cudaSuccess &&
-              (part_floats == 0 || cudaMalloc(&P->tile_part, part_floats * sizeof(float)) == cudaSuccess) &&
-              (n_flags == 0 || cudaMalloc(&P->tile_flag, n_flags * sizeof(unsigned int)) == cudaSuccess) &&
+              cudaMalloc(&P->back_part, (size_t)P->n_tiles * 8 * kTile * kTile * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->tile_part, part_floats * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->tile_flag, n_flags * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc(&P->partials, P->partials_cap * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&P->partials2, P->partials_cap * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&P->tv_sum, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&P->bar, sizeof(Barrier)) == cudaSuccess &&
+              cudaMalloc(&P->phase_ns, 2 * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&P->loop_state, sizeof(mvct_recon_state)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -185,7 +187,9 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     cudaStream_t st = 0;
     cudaError_t e = cudaMemcpy(P->rays, rays.data(), R * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->views, views.data(), g->n_views * sizeof(float4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = launch_fill(P->ones_img, nn, 1.f, st);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaMemset(P->pad[k], 0, pad_floats(g->n) * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(P->pad_ones, 0, pad_floats(g->n) * sizeof(float));
+    if (e == cudaSuccess) e = launch_fill(pad_row0(P->pad_ones, g->n), nn, 1.f, st);
     if (e == cudaSuccess) e = launch_fill(P->sino_tmp, R, 1.f, st);
     if (e == cudaSuccess) e = launch_back(P, P->sino_tmp, P->a1t, -1, st); // A^T 1
     if (e == cudaSuccess) e = cudaMemset(P->bar, 0, sizeof(Barrier));
@@ -213,8 +217,9 @@ extern "C" int mvct_forward(mvct_plan P, const float *d_img, float *d_sino, int3
     if (!d_img || !d_sino) return mvct_fail(MVCT_EINVAL, "mvct_forward: null device pointer");
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
-    CK(launch_transpose(d_img, P->imgT, P->geo.n, st));
-    CK(launch_forward(P, d_img, P->imgT, d_sino, subset, nullptr, nullptr, nullptr, st));
+    float *img = pad_row0(P->pad[0], P->geo.n), *imgT = pad_row0(P->pad[2], P->geo.n);
+    CK(launch_pad_transpose(d_img, img, imgT, P->geo.n, st));
+    CK(launch_forward(P, img, imgT, d_sino, subset, nullptr, nullptr, nullptr, st));
     return MVCT_OK;
 }
 
@@ -252,8 +257,9 @@ extern "C" int mvct_objective(mvct_plan P, const float *d_img, const float *d_si
         return mvct_fail(MVCT_EINVAL, "mvct_objective: invalid beta/eps");
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
-    CK(launch_transpose(d_img, P->imgT, P->geo.n, st));
-    CK(launch_residual(P, d_img, P->imgT, d_sino, d_weights, P->partials, st));
+    float *img = pad_row0(P->pad[0], P->geo.n), *imgT = pad_row0(P->pad[2], P->geo.n);
+    CK(launch_pad_transpose(d_img, img, imgT, P->geo.n, st));
+    CK(launch_residual(P, img, imgT, d_sino, d_weights, P->partials, st));
     CK(launch_tv(P, d_img, (float)eps, nullptr, P->partials2, st));
     CK(launch_final_sum(P->partials, P->reduce_grid, 0.5, P->partials2, P->reduce_grid, beta, d_out, st));
     return MVCT_OK;

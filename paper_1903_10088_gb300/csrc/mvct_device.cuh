@@ -4,11 +4,10 @@
 //                     (Sec. 4.4 "reprojection"): lanes walk consecutive samples
 //                     along the driving axis, so the two interpolation taps of a
 //                     warp step hit one or two 128-byte rows of the image.
-//  * gather_pixel  -- the matched adjoint (Sec. 4.4 "estimation") evaluated per
-//                     pixel: for every view of the subset only the channels whose
-//                     ray passes within one pixel of the pixel centre can carry a
-//                     non-zero Joseph weight; their weights are recomputed from
-//                     the same ray table the projector uses. No atomics.
+//  * splat_views   -- the matched adjoint (Sec. 4.4 "estimation") of one subset
+//                     on a 32x32 pixel tile: each ray that can reach the tile is
+//                     walked across it with the projector's own weights into
+//                     warp-private shared-memory tiles. No atomics.
 //  * tv_grad_pixel -- gradient of the smoothed isotropic TV (Sec. 2).
 //  * grid_sync     -- grid-wide barrier of the persistent loop with a bounded
 //                     wait (global timer limit plus a spin cap).
@@ -62,6 +61,24 @@ __device__ __forceinline__ double warp_sum(double v)
     return v;
 }
 
+// floor(u) for |u| < 2^22 without conversion instructions: adding 1.5 * 2^23
+// with round-toward-minus-infinity leaves floor(u) in the low mantissa bits of
+// the sum (the spacing there is 1). Returns floor(u) as int and u - floor(u).
+// The projector and the backprojection both use it, so their taps and weights
+// agree bit for bit.
+__device__ __forceinline__ int floor_frac(float u, float &frac)
+{
+    const float t = __fadd_rd(u, 12582912.0f);
+    frac = u - (t - 12582912.0f);
+    return __float_as_int(t) - 0x4B400000;
+}
+
+// Images used by the projector carry kPadRows zero rows above and below
+// (row-major, width n): row index r of the image is stored at (r + kPadRows) * n.
+// A tap row clamped into [-kPadRows, n + kPadRows - 1] therefore needs no bounds
+// test: every clamped tap lands on a zero row, exactly like a tap outside the image.
+constexpr int kPadRows = 2;
+
 // Joseph line integral of one ray, computed by the whole warp (all lanes return
 // the same value). img is row-major; imgT is its transpose: a y-driven ray walks
 // the rows of img, which are the columns of imgT, so reading imgT keeps the
@@ -71,10 +88,11 @@ template <bool RO>
 __device__ __forceinline__ float joseph_warp(const float *img, const float *imgT, int n, float pc,
                                              float4 r, int lane)
 {
+    // img / imgT point at row 0 of zero-row-padded buffers (see kPadRows)
     const float *src = (r.w > 0.5f) ? img : imgT;
     const float uc = r.x, m = r.y;
-    // Samples whose taps can fall inside the image: u(p) in (-1, n). The bounds
-    // are widened by one sample; every tap is still bounds-checked below.
+    // Samples whose taps can fall inside the image: u(p) in (-1, n), widened by
+    // one sample (taps outside land on the zero rows).
     int p_lo = 0, p_hi = n - 1;
     if (m != 0.f) {
         float a = __fdividef(-1.f - uc, m), b = __fdividef((float)n - uc, m);
@@ -84,58 +102,33 @@ __device__ __forceinline__ float joseph_warp(const float *img, const float *imgT
     } else if (!(uc > -1.f && uc < (float)n)) {
         p_hi = -1;
     }
+    const int rmin = -kPadRows, rmax = n + kPadRows - 2;
+    // Eight samples per lane per step, all sixteen taps loaded before use.
+    constexpr int U = 8;
     float acc = 0.f;
-    for (int p = p_lo + lane; p <= p_hi; p += 32) {
-        const float u = fmaf(m, (float)p - pc, uc);
-        const float fl = floorf(u);
-        const int i0 = (int)fl;
-        const float f = u - fl;
-        const float a = ((unsigned)i0 < (unsigned)n) ? ldf<RO>(src + (size_t)i0 * n + p) : 0.f;
-        const float b = ((unsigned)(i0 + 1) < (unsigned)n) ? ldf<RO>(src + (size_t)(i0 + 1) * n + p) : 0.f;
+    int p = p_lo + lane;
+    float pf = (float)p - pc;
+    for (; p + (U - 1) * 32 <= p_hi; p += U * 32, pf += (float)(U * 32)) {
+        float f[U], ta[U], tb[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+            const float u = fmaf(m, pf + (float)(q * 32), uc);
+            const int i0 = min(max(floor_frac(u, f[q]), rmin), rmax);
+            const float *t = src + (i0 * n + p + q * 32);
+            ta[q] = ldf<RO>(t);
+            tb[q] = ldf<RO>(t + n);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) acc += fmaf(f[q], tb[q] - ta[q], ta[q]);
+    }
+    for (; p <= p_hi; p += 32, pf += 32.f) {
+        float f;
+        const int i0 = min(max(floor_frac(fmaf(m, pf, uc), f), rmin), rmax);
+        const float *t = src + (i0 * n + p);
+        const float a = ldf<RO>(t), b = ldf<RO>(t + n);
         acc += fmaf(f, b - a, a);
     }
     return warp_sum(acc) * r.z;
-}
-
-// sum_k sum_c A[(v_k, c), (i, j)] * val[k*C + c] over the rows k of a subset
-// (subset < 0: all views). PRESCALED: val already carries the ray's scale.
-// RO: val may be read through the read-only cache.
-template <bool PRESCALED, bool RO>
-__device__ __forceinline__ float gather_pixel(const Geo &g, const float4 *__restrict__ rays,
-                                              const float4 *__restrict__ views, const float *val,
-                                              int i, int j, int subset, int rows)
-{
-    const float fic = (float)i - g.pc, fjc = (float)j - g.pc; // centred indices (exact)
-    const float fi = (float)i, fj = (float)j;
-    const float x = fjc * g.delta, y = fic * g.delta;          // pixel centre (cm)
-    const float d2 = g.delta * g.delta;
-    const float hw_scale = g.delta * g.inv_dgamma;
-    float acc = 0.f;
-    for (int k = 0; k < rows; ++k) {
-        const int v = subset < 0 ? k : subset + k * g.S;
-        const float4 vw = __ldg(&views[v]);
-        const float px = x - vw.x, py = y - vw.y;
-        const float dot = fmaf(px, vw.z, py * vw.w);   // along the central ray (> 0)
-        const float crs = fmaf(vw.z, py, -vw.w * px);  // across it
-        // channel coordinate of the ray through the pixel centre
-        const float cc = fmaf(atanf(__fdividef(crs, dot)), g.inv_dgamma, g.c_mid);
-        // a ray with a non-zero weight passes within delta of the centre, i.e.
-        // within asin(delta/dist) <= delta/sqrt(dist^2 - delta^2) of its angle
-        const float hw = fmaf(hw_scale, rsqrtf(fmaxf(fmaf(dot, dot, fmaf(crs, crs, -d2)), 1e-30f)), 0.02f);
-        const int c0 = max(0, (int)ceilf(fmaxf(cc - hw, -1.f)));
-        const int c1 = min(g.C - 1, (int)floorf(fminf(cc + hw, (float)g.C)));
-        const float4 *rr = rays + (size_t)v * g.C;
-        const float *vv = val + (size_t)k * g.C;
-        for (int c = c0; c <= c1; ++c) {
-            const float4 r = __ldg(&rr[c]);
-            const bool xd = r.w > 0.5f;
-            const float u = fmaf(r.y, xd ? fjc : fic, r.x);
-            const float wgt = fmaxf(0.f, 1.f - fabsf(u - (xd ? fi : fj)));
-            const float s = ldf<RO>(vv + c);
-            acc = fmaf(wgt, PRESCALED ? s : s * r.z, acc);
-        }
-    }
-    return acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -188,37 +181,47 @@ __device__ __forceinline__ int2 tile_window(const Geo &g, float4 vw, int i_lo, i
     return make_int2(c0, c1);
 }
 
+// Staging of a view's rays for the splat: (u_c, m, path length x value, flag).
+// StageE4: the loop kernel's per-subset buffer, already in that form.
+// StageSino: the ray table plus a sinogram row, read through the read-only cache.
+struct StageE4 {
+    const float4 *row; // e4 + k*C
+    __device__ __forceinline__ float4 operator()(int c) const { return row[c]; }
+};
+struct StageSino {
+    const float4 *rays; // ray table row of the view: rays + v*C
+    const float *vals;  // sinogram row: sino + k*C
+    __device__ __forceinline__ float4 operator()(int c) const
+    {
+        const float4 r = __ldg(rays + c);
+        return make_float4(r.x, r.y, r.z * __ldg(vals + c), r.w);
+    }
+};
+
 // Splat channels [c0, c1] of one view onto the warp's accumulator tile.
-// e4row[c] = (u_c, m, prescaled residual, x-driven flag) of the view's rays.
-// pj = j_lo + lane - pc, pi = i_lo + lane - pc. RO: e4row may use the
-// read-only cache (not when it was written earlier in the same kernel).
-template <bool MIRROR, bool RO>
-__device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const float4 *e4row, int c0,
+// pj = j_lo + lane - pc, pi = i_lo + lane - pc.
+template <bool MIRROR, class Stage>
+__device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const Stage &load, int c0,
                                                int c1, float pj, float pi, int i_lo, int j_lo, int lane)
 {
     for (int cb = c0; cb <= c1; cb += 32) {
         const int c = cb + lane;
-        if (c <= c1) {
-            if constexpr (RO) stage[lane] = __ldg(e4row + c);
-            else stage[lane] = e4row[c];
-        }
+        if (c <= c1) stage[lane] = load(c);
         __syncwarp();
         const int cnt = min(32, c1 - cb + 1);
         for (int t = 0; t < cnt; ++t) {
             const float4 r = stage[t];
             if (r.w > 0.5f) { // x-driven: this lane's column, rows a and a+1
-                const float u = fmaf(r.y, pj, r.x);
-                const float fl = floorf(u);
-                const int a = (int)fl - i_lo;
-                const float w1 = (u - fl) * r.z, w0 = r.z - w1;
+                float f;
+                const int a = floor_frac(fmaf(r.y, pj, r.x), f) - i_lo;
+                const float w1 = f * r.z, w0 = r.z - w1;
                 const int col = MIRROR ? (kTile - 1) - lane : lane;
                 if ((unsigned)a < (unsigned)kTile) acc[a * kAccStride + col] += w0;
                 if ((unsigned)(a + 1) < (unsigned)kTile) acc[(a + 1) * kAccStride + col] += w1;
             } else {          // y-driven: this lane's row, columns a and a+1
-                const float u = fmaf(r.y, pi, r.x);
-                const float fl = floorf(u);
-                const int a = (int)fl - j_lo;
-                const float w1 = (u - fl) * r.z, w0 = r.z - w1;
+                float f;
+                const int a = floor_frac(fmaf(r.y, pi, r.x), f) - j_lo;
+                const float w1 = f * r.z, w0 = r.z - w1;
                 float *row = acc + lane * kAccStride;
                 if ((unsigned)a < (unsigned)kTile) row[MIRROR ? (kTile - 1) - a : a] += w0;
                 if ((unsigned)(a + 1) < (unsigned)kTile) row[MIRROR ? (kTile - 2) - a : a + 1] += w1;
@@ -226,6 +229,63 @@ __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const 
         }
         __syncwarp();
     }
+}
+
+// Each view's channel window is cut into this many parts, dealt to warps.
+constexpr int kParts = 2;
+// Largest number of view groups (blocks) that share one tile in the loop.
+constexpr int kMaxGroups = 8;
+
+// One block splats the subset rows k = ka, ka + kstep, ... (< kb) onto the 32x32
+// tile (i_lo, j_lo).
+// Parts of views whose ray slopes are >= 0 go round-robin to warps [0, wpos), the
+// others to warps [wpos, nw) (mirrored layout), wpos = nw/2 (a class without
+// views leaves its warps idle). Returns wpos; after the closing block barrier the
+// tile sum of pixel idx is tile_sum(s_acc, idx, nw, wpos).
+template <class MakeStage>
+__device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restrict__ views, int subset,
+                                           int ka, int kb, int kstep, int i_lo, int j_lo,
+                                           float (*s_acc)[kAccFloats], float4 (*s_stage)[32],
+                                           const MakeStage &make_stage)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = blockDim.x >> 5;
+    const int wpos = nw / 2;
+    const bool mirror = warp >= wpos;
+    const int nmine = mirror ? nw - wpos : wpos;
+    const int q = mirror ? warp - wpos : warp;
+    float *acc = s_acc[warp];
+    float4 *stage = s_stage[warp];
+    const float pj = (float)(j_lo + lane) - g.pc, pi = (float)(i_lo + lane) - g.pc;
+    for (int k = lane; k < kAccFloats; k += 32) acc[k] = 0.f;
+    __syncwarp();
+    int cnt = 0;
+    for (int k = ka; k < kb; k += kstep) {
+        const int v = subset < 0 ? k : subset + k * g.S;
+        const float4 vw = __ldg(&views[v]);
+        if ((vw.z * vw.w < 0.f) != mirror) continue; // slope class of the view
+        for (int part = 0; part < kParts; ++part, ++cnt) {
+            if (cnt % nmine != q) continue;
+            const int2 win = tile_window(g, vw, i_lo, j_lo, lane);
+            const int len = win.y - win.x + 1;
+            const int c0 = win.x + (part * len) / kParts, c1 = win.x + ((part + 1) * len) / kParts - 1;
+            if (c1 < c0) continue;
+            const auto st = make_stage(k, v);
+            if (mirror) splat_channels<true>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
+            else splat_channels<false>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
+        }
+    }
+    __syncthreads();
+    return wpos;
+}
+
+// Block sum of tile pixel idx = ii*32 + jj (see splat_views), warps in order.
+__device__ __forceinline__ float tile_sum(float (*s_acc)[kAccFloats], int idx, int nw, int wpos)
+{
+    const int ii = idx >> 5, jj = idx & 31;
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v += s_acc[w][ii * kAccStride + (w >= wpos ? (kTile - 1) - jj : jj)];
+    return v;
 }
 
 // d/dmu[i][j] of TV_eps = sum sqrt(dx^2 + dy^2 + eps) with forward differences
@@ -262,10 +322,11 @@ __device__ __forceinline__ float tv_grad_pixel(const float *img, int n, int i, i
 // Grid barrier with a bounded wait.
 // ---------------------------------------------------------------------------
 struct Barrier {
-    unsigned int count;   // arrivals at the current barrier
-    unsigned int gen;     // barrier generation
+    unsigned int count;   // arrivals since launch (monotonic; barrier k completes at (k+1)*G)
+    unsigned int pad0[31];
     int err;              // 1: a block gave up waiting (timeout)
     int data_err;         // 1: non-finite / negative input detected in set-up
+    unsigned int pad1[30];
 };
 
 __device__ __forceinline__ unsigned long long global_ns()
@@ -282,46 +343,53 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned int ld_relaxed(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_release(unsigned int *p, unsigned int v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Every block calls this with the same `expected` (the grid size). Returns false
-// in every thread of the block if any block timed out; the caller then leaves
-// the kernel. The wait ends at timeout_ns of global time or after spin_cap polls
-// (each poll is an L2 round trip plus a short sleep), whichever comes first.
-__device__ __forceinline__ bool grid_sync(Barrier *bar, unsigned int expected,
-                                          unsigned long long timeout_ns,
-                                          unsigned long long spin_cap)
+__device__ __forceinline__ void add_release(unsigned int *p, unsigned int v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+// Grid barrier number k (0, 1, 2, ... counted identically by every block): each
+// block adds one arrival with release semantics and polls (relaxed) until the
+// counter reaches (k+1)*G + extra, then takes an acquire fence. extra > 0 makes
+// the barrier unreachable (test knob). Returns false in every thread of the
+// block if the wait hit timeout_ns or spin_cap, or another block already gave
+// up; the caller then leaves the kernel.
+__device__ __forceinline__ bool grid_sync(Barrier *bar, unsigned int k, unsigned int extra,
+                                          unsigned long long timeout_ns, unsigned long long spin_cap)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int gen = ld_acquire(&bar->gen);
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&bar->count, 1u) + 1u;
-        if (arrived == expected) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            st_release(&bar->gen, gen + 1u);
-        } else {
-            const unsigned long long t0 = global_ns();
-            unsigned long long spins = 0;
-            while (ld_acquire(&bar->gen) == gen) {
-                if (*(volatile int *)&bar->err) { ok = 0; break; }
-                ++spins;
-                if (spins > spin_cap ||
-                    ((spins & 31u) == 0 && global_ns() - t0 > timeout_ns)) {
-                    atomicExch(&bar->err, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(40);
+        const unsigned int target = (k + 1u) * gridDim.x + extra;
+        add_release(&bar->count, 1u);
+        unsigned long long spins = 0, t0 = 0;
+        while ((int)(ld_relaxed(&bar->count) - target) < 0) {
+            if (*(volatile int *)&bar->err) { ok = 0; break; }
+            ++spins;
+            if (spins == 64) t0 = global_ns();
+            if (spins > spin_cap || (spins > 64 && (spins & 15u) == 0 && global_ns() - t0 > timeout_ns)) {
+                atomicExch(&bar->err, 1);
+                ok = 0;
+                break;
             }
+            if (spins > 16) __nanosleep(20);
         }
-        __threadfence();
+        fence_acquire();
         if (*(volatile int *)&bar->err) ok = 0;
         s_ok = ok;
     }

@@ -6,21 +6,27 @@
 
 namespace mvct {
 
-// 32x32 tiled transpose through shared memory (padded against bank conflicts).
-__global__ void __launch_bounds__(kThreads) k_transpose(const float *__restrict__ src,
-                                                        float *__restrict__ dst, int n)
+// Copy an n x n image into a zero-row-padded buffer and its transpose into
+// another (both pointers at row 0), 32x32 tiles through shared memory.
+__global__ void __launch_bounds__(kThreads) k_pad_transpose(const float *__restrict__ src,
+                                                            float *__restrict__ dst,
+                                                            float *__restrict__ dstT, int n)
 {
     __shared__ float tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5; // 32 x 8 threads
     for (int r = ty; r < 32; r += 8) {
         const int i = by + r, j = bx + tx;
-        if (i < n && j < n) tile[r][tx] = __ldg(src + (size_t)i * n + j);
+        if (i < n && j < n) {
+            const float v = __ldg(src + (size_t)i * n + j);
+            tile[r][tx] = v;
+            dst[(size_t)i * n + j] = v;
+        }
     }
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
-        const int i = bx + r, j = by + tx; // dst row = src column
-        if (i < n && j < n) dst[(size_t)i * n + j] = tile[tx][r];
+        const int i = bx + r, j = by + tx; // dstT row = src column
+        if (i < n && j < n) dstT[(size_t)i * n + j] = tile[tx][r];
     }
 }
 
@@ -79,34 +85,84 @@ k_residual(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img
     }
 }
 
-// One thread per pixel (grid-stride): img[i][j] = sum over the subset's rays.
+// Stand-alone matched backprojection as a tile splat: block = (tile t, view
+// group h) with t = blockIdx.x % T, h = blockIdx.x / T; group h takes the rows
+// h, h + H, h + 2H, ... With one group the tile
+// is written straight into the image; otherwise each group writes its partial
+// tile and k_merge_tiles adds the groups in order (deterministic).
 __global__ void __launch_bounds__(kThreads)
-k_back(Geo g, const float4 *__restrict__ rays, const float4 *__restrict__ views,
-       const float *__restrict__ sino, float *__restrict__ img, int subset, int rows)
+k_back_splat(Geo g, const float4 *__restrict__ rays, const float4 *__restrict__ views,
+             const float *__restrict__ sino, int subset, int rows, int H, int tiles_x,
+             float *__restrict__ img, float *__restrict__ part)
 {
-    const int nn = g.n * g.n;
-    for (int r = blockIdx.x * kThreads + threadIdx.x; r < nn; r += gridDim.x * kThreads) {
-        const int i = r / g.n, j = r - i * g.n;
-        img[r] = gather_pixel<false, true>(g, rays, views, sino, i, j, subset, rows);
+    __shared__ float s_acc[kWarps][kAccFloats];
+    __shared__ float4 s_stage[kWarps][32];
+    const int T = tiles_x * tiles_x;
+    const int t = blockIdx.x % T, h = blockIdx.x / T;
+    const int i_lo = (t / tiles_x) * kTile, j_lo = (t % tiles_x) * kTile;
+    const int C = g.C;
+    const int wpos = splat_views(g, views, subset, h, rows, H, i_lo, j_lo, s_acc, s_stage,
+                                 [rays, sino, C](int k, int v) {
+                                     return StageSino{rays + (size_t)v * C, sino + (size_t)k * C};
+                                 });
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int idx = threadIdx.x + u * kThreads;
+        const float val = tile_sum(s_acc, idx, kWarps, wpos);
+        if (H == 1) {
+            const int i = i_lo + (idx >> 5), j = j_lo + (idx & 31);
+            if (i < g.n && j < g.n) img[(size_t)i * g.n + j] = val;
+        } else {
+            part[((size_t)t * H + h) * (kTile * kTile) + idx] = val;
+        }
     }
 }
 
-// Set-up of the loop: D = 1/(A^T(w .* A1) + cb) on the support (a1t > 0), else 0;
-// mu0 = support ? (init_from_input ? mu : mu0) : 0, written with its transpose.
+// img = sum over groups h (in order) of the partial tiles.
 __global__ void __launch_bounds__(kThreads)
-k_setup_back(Geo g, const float4 *__restrict__ rays, const float4 *__restrict__ views,
-             const float *__restrict__ wa1, const float *__restrict__ a1t, float cb, float mu0,
-             int init_from_input, float *__restrict__ D, float *mu, float *__restrict__ muT)
+k_merge_tiles(const float *__restrict__ part, int H, int tiles_x, int n, float *__restrict__ img)
 {
-    const int nn = g.n * g.n;
-    for (int r = blockIdx.x * kThreads + threadIdx.x; r < nn; r += gridDim.x * kThreads) {
-        const int i = r / g.n, j = r - i * g.n;
-        const float den = gather_pixel<false, true>(g, rays, views, wa1, i, j, -1, g.V) + cb;
-        const bool on = __ldg(a1t + r) > 0.f && den > 0.f;
-        D[r] = on ? 1.f / den : 0.f;
-        const float m0 = on ? (init_from_input ? mu[r] : mu0) : 0.f;
-        mu[r] = m0;
-        muT[(size_t)j * g.n + i] = m0;
+    const int t = blockIdx.x;
+    const int i_lo = (t / tiles_x) * kTile, j_lo = (t % tiles_x) * kTile;
+    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+        float v = 0.f;
+        for (int h = 0; h < H; ++h) v += part[((size_t)t * H + h) * (kTile * kTile) + idx];
+        const int i = i_lo + (idx >> 5), j = j_lo + (idx & 31);
+        if (i < n && j < n) img[(size_t)i * n + j] = v;
+    }
+}
+
+// Set-up of the loop from the merged A^T(w .* A1) partial tiles:
+// D = 1/(A^T(w .* A1) + cb) on the support (a1t > 0), else 0;
+// mu0 = support ? (init_from_input ? init : mu0) : 0, written with its transpose.
+__global__ void __launch_bounds__(kThreads)
+k_setup_merge(const float *__restrict__ part, int H, int tiles_x, int n, const float *__restrict__ a1t,
+              float cb, float mu0, int init_from_input, const float *__restrict__ init,
+              float *__restrict__ D, float *__restrict__ mu, float *__restrict__ muT)
+{
+    __shared__ float tile[kTile][kTile + 1];
+    const int t = blockIdx.x;
+    const int i_lo = (t / tiles_x) * kTile, j_lo = (t % tiles_x) * kTile;
+    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+        float den = cb;
+        float v = 0.f;
+        for (int h = 0; h < H; ++h) v += part[((size_t)t * H + h) * (kTile * kTile) + idx];
+        den += v;
+        const int ii = idx >> 5, jj = idx & 31, i = i_lo + ii, j = j_lo + jj;
+        float m0 = 0.f;
+        if (i < n && j < n) {
+            const size_t r = (size_t)i * n + j;
+            const bool on = __ldg(a1t + r) > 0.f && den > 0.f;
+            D[r] = on ? 1.f / den : 0.f;
+            m0 = on ? (init_from_input ? __ldg(init + r) : mu0) : 0.f;
+            mu[r] = m0;
+        }
+        tile[ii][jj] = m0;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kTile * kTile; idx += kThreads) {
+        const int jj = idx >> 5, ii = idx & 31, i = i_lo + ii, j = j_lo + jj;
+        if (i < n && j < n) muT[(size_t)j * n + i] = tile[ii][jj];
     }
 }
 
@@ -166,16 +222,10 @@ static int ray_grid(const mvct_plan_s *P, long long rays)
     return (int)std::max<long long>(1, std::min<long long>(want, (long long)P->num_sms * 16));
 }
 
-static int pixel_grid(const mvct_plan_s *P, long long pixels)
-{
-    const long long want = (pixels + kThreads - 1) / kThreads;
-    return (int)std::max<long long>(1, std::min<long long>(want, (long long)P->num_sms * 16));
-}
-
-cudaError_t launch_transpose(const float *src, float *dst, int n, cudaStream_t st)
+cudaError_t launch_pad_transpose(const float *src, float *dst, float *dstT, int n, cudaStream_t st)
 {
     dim3 grid((n + 31) / 32, (n + 31) / 32);
-    k_transpose<<<grid, kThreads, 0, st>>>(src, dst, n);
+    k_pad_transpose<<<grid, kThreads, 0, st>>>(src, dst, dstT, n);
     return cudaGetLastError();
 }
 
@@ -196,19 +246,34 @@ cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float 
     return cudaGetLastError();
 }
 
+// View groups per tile for the stand-alone splat: enough blocks to fill the GPU
+// a few times over, at most 8 and at most one group per view.
+static int back_groups(const mvct_plan_s *P, int rows)
+{
+    const int want = (4 * P->num_sms * 4 + P->n_tiles - 1) / P->n_tiles;
+    return std::max(1, std::min(std::min(8, rows), want));
+}
+
 cudaError_t launch_back(const mvct_plan_s *P, const float *sino, float *img, int subset,
                         cudaStream_t st)
 {
-    k_back<<<pixel_grid(P, (long long)P->geo.n * P->geo.n), kThreads, 0, st>>>(
-        P->geo, P->rays, P->views, sino, img, subset, rows_of(P, subset));
+    const int rows = rows_of(P, subset);
+    const int H = back_groups(P, rows);
+    k_back_splat<<<P->n_tiles * H, kThreads, 0, st>>>(P->geo, P->rays, P->views, sino, subset, rows, H,
+                                                      P->tiles_x, img, P->back_part);
+    if (H > 1) k_merge_tiles<<<P->n_tiles, kThreads, 0, st>>>(P->back_part, H, P->tiles_x, P->geo.n, img);
     return cudaGetLastError();
 }
 
 cudaError_t launch_setup_back(const mvct_plan_s *P, const float *wa1, float cb, float mu0,
-                              int init_from_input, float *mu, float *muT, cudaStream_t st)
+                              int init_from_input, const float *init, float *mu, float *muT,
+                              cudaStream_t st)
 {
-    k_setup_back<<<pixel_grid(P, (long long)P->geo.n * P->geo.n), kThreads, 0, st>>>(
-        P->geo, P->rays, P->views, wa1, P->a1t, cb, mu0, init_from_input, P->D, mu, muT);
+    const int H = back_groups(P, P->geo.V);
+    k_back_splat<<<P->n_tiles * H, kThreads, 0, st>>>(P->geo, P->rays, P->views, wa1, -1, P->geo.V, H,
+                                                      P->tiles_x, nullptr, P->back_part);
+    k_setup_merge<<<P->n_tiles, kThreads, 0, st>>>(P->back_part, H, P->tiles_x, P->geo.n, P->a1t, cb, mu0,
+                                                   init_from_input, init, P->D, mu, muT);
     return cudaGetLastError();
 }
 

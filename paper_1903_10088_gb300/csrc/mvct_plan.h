@@ -16,22 +16,25 @@ struct mvct_plan_s {
     float4 *rays = nullptr;     // [V*C] ray table (see mvct_device.cuh)
     float4 *views = nullptr;    // [V] source point and central direction
     float *a1t = nullptr;       // [n*n] A^T 1 over all views (support mask = a1t > 0)
-    float *ones_img = nullptr;  // [n*n] all ones (its own transpose)
-    float *imgT = nullptr;      // [n*n] transpose scratch of the stand-alone projector
+    // Zero-row-padded images ((n + 2*kPadRows) rows of n floats; the pointers
+    // below address the allocation, row 0 of the image is at + kPadRows*n):
+    // pad[0], pad[1] the loop's ping-pong image, pad[2], pad[3] their transposes;
+    // pad[0] and pad[2] double as the stand-alone projector's copies.
+    float *pad[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *pad_ones = nullptr;  // padded all-ones image (its own transpose)
     float *sino_tmp = nullptr;  // [V*C] set-up scratch
-    float *mu1 = nullptr;       // [n*n] second image buffer of the loop
-    float *muT0 = nullptr;      // [n*n] transposes of the two loop buffers
-    float *muT1 = nullptr;
     float *D = nullptr;         // [n*n] surrogate diagonal (0 off the support)
     float4 *e4 = nullptr;       // [Vs*C] (u_c, m, prescaled weighted residual, flag) of one subset
-    float *tile_part = nullptr; // [n_tiles][groups-1][32*32] partial tile backprojections
-    unsigned int *tile_flag = nullptr; // [n_tiles][groups-1] publication stamps
+    float *tile_part = nullptr; // [n_tiles][groups][32*32] partial tiles of the loop's phase B
+    float *back_part = nullptr; // [n_tiles][8][32*32] partial tiles of the stand-alone backprojection
+    unsigned int *tile_flag = nullptr; // [n_tiles][groups] publication stamps
     int tiles_x = 0, n_tiles = 0, groups = 1; // phase-B decomposition of the loop kernel
     double *partials = nullptr; // [partials_cap] per-block FP64 partial sums
     double *partials2 = nullptr;
     int partials_cap = 0;
     double *tv_sum = nullptr;   // [1] scratch scalar
     mvct::Barrier *bar = nullptr;
+    unsigned long long *phase_ns = nullptr; // [2] loop phase timers
     void *loop_state = nullptr; // device copy of the resume state
     double *hist = nullptr;     // [2*hist_cap] phi and lambda per sub-iteration
     double *sched = nullptr;    // [hist_cap] lambda schedule
@@ -47,7 +50,7 @@ constexpr int kWarps = kThreads / 32;
 
 // Stand-alone launchers (mvct_kernels.cu). All enqueue on `st` and return the
 // launch status.
-cudaError_t launch_transpose(const float *src, float *dst, int n, cudaStream_t st);
+cudaError_t launch_pad_transpose(const float *src, float *dst, float *dstT, int n, cudaStream_t st);
 cudaError_t launch_forward(const mvct_plan_s *P, const float *img, const float *imgT, float *out,
                            int subset, const float *mul, const float *check_p, int *data_err,
                            cudaStream_t st);
@@ -62,8 +65,13 @@ cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float 
 cudaError_t launch_final_sum(const double *a, int na, double ca, const double *b, int nb, double cb,
                              double *out, cudaStream_t st);
 cudaError_t launch_setup_back(const mvct_plan_s *P, const float *wa1, float cb, float mu0,
-                              int init_from_input, float *mu, float *muT, cudaStream_t st);
+                              int init_from_input, const float *init, float *mu, float *muT,
+                              cudaStream_t st);
 cudaError_t launch_fill(float *dst, size_t count, float value, cudaStream_t st);
+
+// Row 0 of a zero-row-padded image buffer.
+inline float *pad_row0(float *buf, int n) { return buf + (size_t)kPadRows * n; }
+inline size_t pad_floats(int n) { return (size_t)(n + 2 * kPadRows) * n; }
 
 // Persistent loop (mvct_recon.cu).
 int recon_occupancy(mvct_plan_s *P);

@@ -14,6 +14,7 @@
 //   barrier
 // The image ping-pongs between the caller's buffer and a plan buffer; the
 // transpose copy lets y-driven rays read contiguous memory.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -21,6 +22,9 @@
 #include "mvct_plan.h"
 
 namespace mvct {
+
+// Largest persistent grid (8 co-resident blocks on each of up to 160 SMs).
+#define MVCT_MAX_RECON_GRID 1280
 
 struct ReconArgs {
     Geo g;
@@ -33,7 +37,7 @@ struct ReconArgs {
     float *muT0, *muT1; // and their transposes
     float4 *e4;         // [Vs*C] (u_c, m, prescaled residual, flag) of the subset's rays
     double *partials;
-    float *tile_part;   // [T][H-1][1024] partial backprojections of the non-owner groups
+    float *tile_part;   // [T][H-1][1024] partial tiles of the non-owner view groups
     unsigned int *tile_flag; // [T][H-1] sub-iteration stamp of each published partial
     float *best;
     double *phi_hist;
@@ -41,9 +45,10 @@ struct ReconArgs {
     const double *sched;
     mvct_recon_state *st;
     Barrier *bar;
+    unsigned long long *phase_ns; // [2] block 0's time in phase F (+ barrier 1) and phase B (+ barrier 2)
     long long n0;
     int n_iter;
-    int tiles_x, n_tiles, groups; // phase B work: n_tiles x groups items
+    int tiles_x, n_tiles, groups; // phase B: 32x32 tiles x view groups
     double lambda0, dup, ddown, lmin, kappa;
     float beta, eps;
     unsigned long long timeout_ns, spin_cap;
@@ -99,15 +104,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
     __syncthreads();
 
     const int Rs = g.Vs * g.C;
-    const int H = a.groups;
-    const int n_items = a.n_tiles * H;
-    const int n_nonowner = a.n_tiles * (H - 1);
     const float S_f = (float)g.S;
-    // warps 0..3 take the views whose ray slopes are >= 0, warps 4..7 the others
-    const bool mirror = warp >= kWarps / 2;
-    const int q = warp & (kWarps / 2 - 1);
-    float *acc = s_acc[warp];
-    float4 *stage = s_stage[warp];
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_f = 0, t_b = 0, t_mark = timer ? global_ns() : 0;
 
     for (int it = 0; it < a.n_iter; ++it) {
         const long long n = a.n0 + it;
@@ -121,15 +120,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
 
         // ---- phase F: reprojection, residual, square difference -------------
         double acc_phi = 0.0;
-        for (int ray = gw0; ray < Rs; ray += GW) {
-            const int k = ray / g.C, c = ray - k * g.C;
-            const size_t rv = (size_t)(s + k * g.S) * g.C + c;
-            const float4 r = __ldg(&a.rays[rv]);
-            const float q_ray = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
-            if (lane == 0) {
-                const float res = q_ray - __ldg(a.p + rv);
-                a.e4[ray] = make_float4(r.x, r.y, r.z * __ldg(a.w + rv) * res, r.w);
-                acc_phi += (double)res * (double)res;
+        {
+            // the next ray's table entry and data are fetched while this ray is walked
+            float4 r_nx = make_float4(0.f, 0.f, 0.f, 1.f);
+            float p_nx = 0.f, w_nx = 0.f;
+            size_t rv_nx = 0;
+            if (gw0 < Rs) {
+                const int k = gw0 / g.C;
+                rv_nx = (size_t)(s + k * g.S) * g.C + (gw0 - k * g.C);
+                r_nx = __ldg(&a.rays[rv_nx]);
+                if (lane == 0) {
+                    p_nx = __ldg(a.p + rv_nx);
+                    w_nx = __ldg(a.w + rv_nx);
+                }
+            }
+            for (int ray = gw0; ray < Rs; ray += GW) {
+                const float4 r = r_nx;
+                const float pv = p_nx, wv = w_nx;
+                const int nray = ray + GW;
+                if (nray < Rs) {
+                    const int k = nray / g.C;
+                    rv_nx = (size_t)(s + k * g.S) * g.C + (nray - k * g.C);
+                    r_nx = __ldg(&a.rays[rv_nx]);
+                    if (lane == 0) {
+                        p_nx = __ldg(a.p + rv_nx);
+                        w_nx = __ldg(a.w + rv_nx);
+                    }
+                }
+                const float q_ray = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
+                if (lane == 0) {
+                    const float res = q_ray - pv;
+                    a.e4[ray] = make_float4(r.x, r.y, r.z * wv * res, r.w);
+                    acc_phi += (double)res * (double)res;
+                }
             }
         }
         if (lane == 0) s_warp[warp] = acc_phi;
@@ -139,16 +162,47 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
             for (int k = 0; k < kWarps; ++k) t += s_warp[k];
             a.partials[blockIdx.x] = t;
         }
-        const unsigned int expect = G + ((it == 0 && a.debug_unreachable) ? 1u : 0u);
-        if (!grid_sync(a.bar, expect, a.timeout_ns, a.spin_cap)) return;
+        if (!grid_sync(a.bar, 2u * it, (it == 0 && a.debug_unreachable) ? 1u : 0u, a.timeout_ns,
+                       a.spin_cap))
+            return;
+        if (timer) {
+            const unsigned long long now = global_ns();
+            t_f += now - t_mark;
+            t_mark = now;
+        }
 
         // ---- adaptive lambda (Eq. 4-5) and best iterate (Sec. 4.2) ----------
-        if (warp == 0) {
+        // Every block sums the G partials in the same fixed order: each thread
+        // its strided share, then the warp trees, then the warps in order.
+        {
+            // all loads first (one round trip), then the fixed-order sums
+            constexpr int L = (MVCT_MAX_RECON_GRID + kThreads - 1) / kThreads;
+            double v[L];
+#pragma unroll
+            for (int u = 0; u < L; ++u) {
+                const unsigned int b = threadIdx.x + u * kThreads;
+                v[u] = b < G ? a.partials[b] : 0.0;
+            }
             double t = 0.0;
-            for (unsigned int b = lane; b < G; b += 32) t += a.partials[b];
+#pragma unroll
+            for (int u = 0; u < L; ++u) t += v[u];
             t = warp_sum(t);
+            if (lane == 0) s_warp[warp] = t;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double phi = 0.0;
+            for (int k = 0; k < kWarps; ++k) phi += s_warp[k];
+            const int slot_n = (int)(n % g.S);
+            if (lane == 0) s_ring[slot_n] = phi;
+            __syncwarp();
+            // pass sum Phi_{n-S+1} + ... + Phi_n: lane-strided, then the warp tree
+            double pass = 0.0;
+            const bool full = n >= g.S - 1;
+            if (full)
+                for (int k = lane; k < g.S; k += 32) pass += s_ring[k];
+            pass = warp_sum(pass);
             if (lane == 0) {
-                const double phi = t;
                 double lam;
                 if (a.sched) {
                     lam = a.sched[it];
@@ -162,16 +216,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
                 }
                 s_lambda = lam;
                 s_phi_prev = phi;
-                s_ring[n % g.S] = phi;
                 int bf = 0;
-                if (n >= g.S - 1) {
-                    double pass = 0.0;
-                    for (long long k = n - g.S + 1; k <= n; ++k) pass += s_ring[k % g.S];
-                    if (pass < s_best_pass) {
-                        s_best_pass = pass;
-                        s_best_n = n;
-                        bf = 1;
-                    }
+                if (full && pass < s_best_pass) {
+                    s_best_pass = pass;
+                    s_best_n = n;
+                    bf = 1;
                 }
                 s_best_flag = bf;
                 s_tau = (float)(a.kappa * lam);
@@ -184,59 +233,39 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
         __syncthreads();
 
         // ---- phase B: tile splat (estimation) + TV + preconditioned step ----
-        // Items: (tile, view group h). Groups h < H-1 publish a partial tile;
-        // group H-1 (the owner) adds the partials in group order and updates
-        // the tile. Non-owner items come first in every block's sequence, so an
-        // owner only ever waits on items that never wait.
+        // Items: (tile t, view group h), group h holding the subset rows
+        // h, h + H, h + 2H, ... Groups h < H-1 publish a partial tile; group
+        // H-1 (the owner) adds the partials in group order and updates the tile.
+        // Non-owner items come first in every block's sequence, so an owner only
+        // ever waits on items that never wait.
         const float tau = s_tau;
         const bool keep_best = s_best_flag && a.best;
+        const int H = a.groups;
+        const int n_items = a.n_tiles * H, n_nonowner = a.n_tiles * (H - 1);
+        const float4 *e4 = a.e4;
+        const int C = g.C;
         for (int item = blockIdx.x; item < n_items; item += G) {
             const bool owner = item >= n_nonowner;
             const int t = owner ? item - n_nonowner : item % a.n_tiles;
             const int h = owner ? H - 1 : item / a.n_tiles;
             const int i_lo = (t / a.tiles_x) * kTile, j_lo = (t % a.tiles_x) * kTile;
-            const float pj = (float)(j_lo + lane) - g.pc, pi = (float)(i_lo + lane) - g.pc;
-
-            for (int k = lane; k < kAccFloats; k += 32) acc[k] = 0.f;
-            __syncwarp();
-            int cnt = 0;
-            for (int k = h; k < g.Vs; k += H) {
-                const float4 vw = __ldg(&a.views[s + k * g.S]);
-                if ((vw.z * vw.w < 0.f) != mirror) continue; // slope class of the view
-                for (int part = 0; part < 2; ++part, ++cnt) {
-                    if ((cnt & (kWarps / 2 - 1)) != q) continue;
-                    const int2 win = tile_window(g, vw, i_lo, j_lo, lane);
-                    const int mid = (win.x + win.y + 1) >> 1;
-                    const int c0 = part ? mid : win.x, c1 = part ? win.y : mid - 1;
-                    const float4 *row = a.e4 + (size_t)k * g.C;
-                    if (mirror) splat_channels<true, false>(acc, stage, row, c0, c1, pj, pi, i_lo, j_lo, lane);
-                    else splat_channels<false, false>(acc, stage, row, c0, c1, pj, pi, i_lo, j_lo, lane);
-                }
-            }
-            __syncthreads();
-
-            // sum the warps' tiles in warp order: 4 pixels per thread
+            const int wpos = splat_views(g, a.views, s, h, g.Vs, H, i_lo, j_lo, s_acc, s_stage,
+                                         [e4, C](int k, int) { return StageE4{e4 + (size_t)k * C}; });
             float part_val[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int idx = threadIdx.x + u * kThreads;
-                const int ii = idx >> 5, jj = idx & 31;
-                float v = 0.f;
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w)
-                    v += s_acc[w][ii * kAccStride + (w >= kWarps / 2 ? (kTile - 1) - jj : jj)];
-                part_val[u] = v;
-            }
+            for (int u = 0; u < 4; ++u) part_val[u] = tile_sum(s_acc, threadIdx.x + u * kThreads, kWarps, wpos);
 
             if (!owner) {
-                float *dst = a.tile_part + ((size_t)t * (H - 1) + h) * (kTile * kTile);
+                const size_t slot = (size_t)t * (H - 1) + h;
+                float *dst = a.tile_part + slot * (kTile * kTile);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) __stcg(dst + threadIdx.x + u * kThreads, part_val[u]);
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     __threadfence();
-                    st_release(a.tile_flag + (size_t)t * (H - 1) + h, stamp);
+                    st_release(a.tile_flag + slot, stamp);
                 }
+                __syncthreads(); // s_acc is zeroed by the next item
                 continue;
             }
 
@@ -250,14 +279,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
             __syncthreads();
             if (!s_ok) return;
 
+            // partial tiles of groups 0..H-2: all loads first, then the sums in group order
+            float prev[kMaxGroups - 1][4];
+#pragma unroll
+            for (int hh = 0; hh < kMaxGroups - 1; ++hh)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    prev[hh][u] = hh < H - 1 ? __ldcg(a.tile_part + ((size_t)t * (H - 1) + hh) * (kTile * kTile) +
+                                                      threadIdx.x + u * kThreads)
+                                             : 0.f;
             float *tile = s_acc[0]; // reused for the transposed write-out
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int idx = threadIdx.x + u * kThreads;
                 const int ii = idx >> 5, jj = idx & 31;
                 float gs = 0.f;
-                for (int hh = 0; hh < H - 1; ++hh)
-                    gs += __ldcg(a.tile_part + ((size_t)t * (H - 1) + hh) * (kTile * kTile) + idx);
+#pragma unroll
+                for (int hh = 0; hh < kMaxGroups - 1; ++hh)
+                    if (hh < H - 1) gs += prev[hh][u];
                 gs += part_val[u];
                 const int i = i_lo + ii, j = j_lo + jj;
                 float nm = 0.f;
@@ -290,9 +329,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
             }
             __syncthreads(); // tile (s_acc[0]) is zeroed by the next item
         }
-        if (!grid_sync(a.bar, G, a.timeout_ns, a.spin_cap)) return;
+        if (!grid_sync(a.bar, 2u * it + 1u, 0u, a.timeout_ns, a.spin_cap)) return;
+        if (timer) {
+            const unsigned long long now = global_ns();
+            t_b += now - t_mark;
+            t_mark = now;
+        }
     }
 
+    if (timer) {
+        a.phase_ns[0] = t_f;
+        a.phase_ns[1] = t_b;
+    }
     if (blockIdx.x == 0) {
         for (int k = threadIdx.x; k < g.S; k += kThreads) a.st->phi_ring[k] = s_ring[k];
         if (threadIdx.x == 0) {
@@ -310,7 +358,7 @@ int recon_occupancy(mvct_plan_s *P)
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_recon, kThreads, 0) != cudaSuccess)
         return 0;
-    return nb * P->num_sms;
+    return std::min(nb * P->num_sms, MVCT_MAX_RECON_GRID);
 }
 
 } // namespace mvct
@@ -417,17 +465,20 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     if (o.lambda_schedule && n_iter > 0)
         CK(cudaMemcpyAsync(P->sched, o.lambda_schedule, sizeof(double) * n_iter, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
-    if (P->tile_flag)
-        CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * (P->groups - 1), st));
+    CK(cudaMemsetAsync(P->phase_ns, 0, 2 * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups, st));
 
     Events ev;
     CK(cudaEventRecord(ev.e[0], st));
     // set-up (a0): w .* A1 over all views (and input validation), then D and mu0
-    CK(launch_forward(P, P->ones_img, P->ones_img, P->sino_tmp, -1, d_weights, d_sino,
-                      &P->bar->data_err, st));
+    const int n = g.n;
+    float *mu_a = pad_row0(P->pad[0], n), *mu_b = pad_row0(P->pad[1], n);
+    float *muT_a = pad_row0(P->pad[2], n), *muT_b = pad_row0(P->pad[3], n);
+    const float *ones = pad_row0(P->pad_ones, n);
+    CK(launch_forward(P, ones, ones, P->sino_tmp, -1, d_weights, d_sino, &P->bar->data_err, st));
     const double cb = beta * 8.0 / std::sqrt(o.tv_eps);
     CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0,
-                         d_img_inout, P->muT0, st));
+                         d_img_inout, mu_a, muT_a, st));
     CK(cudaEventRecord(ev.e[1], st));
 
     if (n_iter > 0) {
@@ -439,10 +490,10 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         a.p = d_sino;
         a.w = d_weights;
         a.D = P->D;
-        a.mu0 = d_img_inout;
-        a.mu1 = P->mu1;
-        a.muT0 = P->muT0;
-        a.muT1 = P->muT1;
+        a.mu0 = mu_a;
+        a.mu1 = mu_b;
+        a.muT0 = muT_a;
+        a.muT1 = muT_b;
         a.e4 = P->e4;
         a.partials = P->partials;
         a.tile_part = P->tile_part;
@@ -456,6 +507,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         a.sched = o.lambda_schedule ? P->sched : nullptr;
         a.st = (mvct_recon_state *)P->loop_state;
         a.bar = P->bar;
+        a.phase_ns = P->phase_ns;
         a.n0 = hs.n_done;
         a.n_iter = n_iter;
         a.lambda0 = o.lambda0;
@@ -475,13 +527,15 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
             return mvct_fail(MVCT_ELAUNCH, "mvct_recon: %d blocks cannot be co-resident", P->recon_grid);
         if (le != cudaSuccess)
             return mvct_fail(MVCT_ECUDA, "mvct_recon: cooperative launch: %s", cudaGetErrorString(le));
-        if (n_iter & 1)
-            CK(cudaMemcpyAsync(d_img_inout, P->mu1, nn * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
+    CK(cudaMemcpyAsync(d_img_inout, (n_iter & 1) ? mu_b : mu_a, nn * sizeof(float), cudaMemcpyDeviceToDevice,
+                       st));
     CK(cudaEventRecord(ev.e[2], st));
 
     Barrier hb;
     CK(cudaMemcpyAsync(&hb, P->bar, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    unsigned long long hphase[2] = {0, 0};
+    CK(cudaMemcpyAsync(hphase, P->phase_ns, sizeof(hphase), cudaMemcpyDeviceToHost, st));
     mvct_recon_state out_state;
     CK(cudaMemcpyAsync(&out_state, P->loop_state, sizeof(out_state), cudaMemcpyDeviceToHost, st));
     std::vector<double> hist(2 * (size_t)n_iter);
@@ -504,6 +558,8 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         cudaEventElapsedTime(&t2, ev.e[1], ev.e[2]);
         stats->setup_ms = t1;
         stats->loop_ms = t2;
+        stats->forward_ms = hphase[0] * 1e-6;
+        stats->back_ms = hphase[1] * 1e-6;
         stats->grid_blocks = P->recon_grid;
         stats->block_threads = kThreads;
     }

@@ -83,6 +83,8 @@ class ReconStats(ctypes.Structure):
         ("best_pass", ctypes.c_double),
         ("loop_ms", ctypes.c_double),
         ("setup_ms", ctypes.c_double),
+        ("forward_ms", ctypes.c_double),
+        ("back_ms", ctypes.c_double),
         ("grid_blocks", ctypes.c_int32),
         ("block_threads", ctypes.c_int32),
     ]
@@ -158,6 +160,8 @@ class ReconResult:
     loop_ms: float
     setup_ms: float
     grid_blocks: int
+    forward_ms: float = 0.0
+    back_ms: float = 0.0
 
 
 class Plan:
@@ -261,7 +265,7 @@ class Plan:
                                 ctypes.byref(o), _dev_f32(img, self.n * self.n, "img"),
                                 ctypes.byref(st), ctypes.c_void_p(_stream(stream))))
         return img, ReconResult(phi[:n_iter], lam[:n_iter], st.best_n, st.best_pass, st.loop_ms,
-                                st.setup_ms, st.grid_blocks)
+                                st.setup_ms, st.grid_blocks, st.forward_ms, st.back_ms)
 
 
 def tv_grad_noalloc(img: torch.Tensor, eps: float, grad: torch.Tensor, tv: Optional[torch.Tensor] = None,
