@@ -155,6 +155,44 @@ int mvct_recon(mvct_plan plan, const float *d_sino, const float *d_weights, doub
                int32_t n_iter, const mvct_recon_opts *opts, float *d_img_inout,
                mvct_recon_stats *stats, void *stream);
 
+/* ---- Batches: many slices (uneven geometries) in one persistent launch ----
+ * The plans (one per slice, all on one device, each in at most one batch) are
+ * reconstructed together: the co-resident grid is split into block groups, each
+ * group runs the ordered-subset loop of mvct_recon on its own slices with
+ * group-local barriers; blocks are given to groups in proportion to each
+ * slice's work (views/S x channels x n). A plan in a batch may not be passed to
+ * mvct_recon until the batch is destroyed. */
+typedef struct mvct_batch_s *mvct_batch;
+
+/* Create a batch over `count` distinct plans (host array). Synchronous. */
+int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_batch *out);
+
+/* Free a batch (synchronises the device); its plans become usable again. */
+void mvct_batch_destroy(mvct_batch batch);
+
+/* Bind the slices' data (host arrays of `count` entries, in plan order): device
+ * pointers to p and w ([V][C] of each plan's geometry), TV weights beta, and the
+ * images (n*n, in = start image if opts->init_from_input, out = final iterate),
+ * plus the largest n_iter that mvct_batch_run will be given. opts as for
+ * mvct_recon (NULL = defaults); lambda_schedule, state and d_best_out must be
+ * NULL. Synchronous; pointers are kept until the next bind. */
+int mvct_batch_bind(mvct_batch batch, const float *const *d_sinos, const float *const *d_weights,
+                    const double *betas, float *const *d_imgs, int32_t max_iter,
+                    const mvct_recon_opts *opts);
+
+/* Enqueue the set-up of every slice, one persistent cooperative launch running
+ * n_iter sub-iterations on every slice, and the copy of each final image into
+ * its bound buffer. Asynchronous on `stream`: no host synchronisation, no host
+ * memory access. */
+int mvct_batch_run(mvct_batch batch, int32_t n_iter, void *stream);
+
+/* Synchronise the device, then fill *stats (may be NULL) for one slice (plan
+ * order) of the last run: Phi and lambda per sub-iteration, best pass, and the
+ * device times of the whole batch (setup_ms, loop_ms; -1 after a CUDA-graph
+ * replay of mvct_batch_run). Returns MVCT_ETIMEOUT / MVCT_EDATA if the run
+ * failed. */
+int mvct_batch_stats(mvct_batch batch, int32_t slice, mvct_recon_stats *stats);
+
 /* Allocation-free variant of mvct_tv_grad for callers that may not allocate
  * device memory (applications that hand out all GPU memory through their own
  * allocator, or latency-critical paths where cudaMalloc/cudaFree, which can

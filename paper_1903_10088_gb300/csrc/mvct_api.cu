@@ -116,7 +116,8 @@ void free_plan(mvct_plan_s *P)
     if (!P) return;
     void *ptrs[] = {P->rays, P->views, P->a1t, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
                     P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
-                    P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched};
+                    P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched,
+                    P->d_slice, P->d_group, P->d_block_group, P->d_count};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -177,7 +178,11 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
               cudaMalloc(&P->tv_sum, sizeof(double)) == cudaSuccess &&
               cudaMalloc(&P->bar, sizeof(Barrier)) == cudaSuccess &&
               cudaMalloc(&P->phase_ns, 2 * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaMalloc(&P->loop_state, sizeof(mvct_recon_state)) == cudaSuccess;
+              cudaMalloc(&P->loop_state, sizeof(mvct_recon_state)) == cudaSuccess &&
+              cudaMalloc(&P->d_slice, sizeof(SliceDesc)) == cudaSuccess &&
+              cudaMalloc(&P->d_group, sizeof(GroupDesc)) == cudaSuccess &&
+              cudaMalloc(&P->d_block_group, sizeof(int) * std::max(1, P->recon_grid)) == cudaSuccess &&
+              cudaMalloc(&P->d_count, 128) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_plan(P);
@@ -193,6 +198,7 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     if (e == cudaSuccess) e = launch_fill(P->sino_tmp, R, 1.f, st);
     if (e == cudaSuccess) e = launch_back(P, P->sino_tmp, P->a1t, -1, st); // A^T 1
     if (e == cudaSuccess) e = cudaMemset(P->bar, 0, sizeof(Barrier));
+    if (e == cudaSuccess) e = cudaMemset(P->d_block_group, 0, sizeof(int) * std::max(1, P->recon_grid));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         free_plan(P);

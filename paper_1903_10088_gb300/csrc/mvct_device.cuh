@@ -103,8 +103,8 @@ __device__ __forceinline__ float joseph_warp(const float *img, const float *imgT
         p_hi = -1;
     }
     const int rmin = -kPadRows, rmax = n + kPadRows - 2;
-    // Eight samples per lane per step, all sixteen taps loaded before use.
-    constexpr int U = 8;
+    // Four samples per lane per step, all eight taps loaded before use.
+    constexpr int U = 4;
     float acc = 0.f;
     int p = p_lo + lane;
     float pf = (float)p - pc;
@@ -362,35 +362,36 @@ __device__ __forceinline__ void add_release(unsigned int *p, unsigned int v)
 
 __device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
-// Grid barrier number k (0, 1, 2, ... counted identically by every block): each
-// block adds one arrival with release semantics and polls (relaxed) until the
-// counter reaches (k+1)*G + extra, then takes an acquire fence. extra > 0 makes
-// the barrier unreachable (test knob). Returns false in every thread of the
-// block if the wait hit timeout_ns or spin_cap, or another block already gave
-// up; the caller then leaves the kernel.
-__device__ __forceinline__ bool grid_sync(Barrier *bar, unsigned int k, unsigned int extra,
-                                          unsigned long long timeout_ns, unsigned long long spin_cap)
+// Barrier number k (0, 1, 2, ... counted identically by every block) among the
+// nblocks blocks that share `count`: each block adds one arrival with release
+// semantics and polls (relaxed) until the counter reaches (k+1)*nblocks + extra,
+// then takes an acquire fence. extra > 0 makes the barrier unreachable (test
+// knob). Returns false in every thread of the block if the wait hit timeout_ns
+// or spin_cap, or if any block has set *err; the caller then leaves the kernel.
+__device__ __forceinline__ bool group_sync(unsigned int *count, int *err, unsigned int k,
+                                           unsigned int nblocks, unsigned int extra,
+                                           unsigned long long timeout_ns, unsigned long long spin_cap)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned int target = (k + 1u) * gridDim.x + extra;
-        add_release(&bar->count, 1u);
+        const unsigned int target = (k + 1u) * nblocks + extra;
+        add_release(count, 1u);
         unsigned long long spins = 0, t0 = 0;
-        while ((int)(ld_relaxed(&bar->count) - target) < 0) {
-            if (*(volatile int *)&bar->err) { ok = 0; break; }
+        while ((int)(ld_relaxed(count) - target) < 0) {
+            if (*(volatile int *)err) { ok = 0; break; }
             ++spins;
             if (spins == 64) t0 = global_ns();
             if (spins > spin_cap || (spins > 64 && (spins & 15u) == 0 && global_ns() - t0 > timeout_ns)) {
-                atomicExch(&bar->err, 1);
+                atomicExch(err, 1);
                 ok = 0;
                 break;
             }
             if (spins > 16) __nanosleep(20);
         }
         fence_acquire();
-        if (*(volatile int *)&bar->err) ok = 0;
+        if (*(volatile int *)err) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

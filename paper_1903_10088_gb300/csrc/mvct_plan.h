@@ -7,6 +7,55 @@
 #include "mvct.h"
 #include "mvct_device.cuh"
 
+namespace mvct {
+
+// One slice of a loop launch (device copy read by the loop kernel).
+struct SliceDesc {
+    Geo g;
+    const float4 *rays;
+    const float4 *views;
+    const float *p;           // measured log projections [V][C]
+    const float *w;           // statistical weights [V][C]
+    const float *D;           // surrogate diagonal [n][n]
+    float *mu0, *mu1;         // row 0 of the padded ping-pong images
+    float *muT0, *muT1;       // and of their transposes
+    float4 *e4;               // [Vs][C] per-ray (u_c, m, prescaled residual, flag)
+    float *tile_part;         // [n_tiles][groups-1][32*32] partial tiles
+    unsigned int *tile_flag;  // [n_tiles][groups-1] publication stamps
+    float *best;              // best iterate (or null)
+    double *phi_hist;         // [n_iter]
+    double *lam_hist;         // [n_iter]
+    const double *sched;      // lambda replay schedule (or null)
+    mvct_recon_state *st;     // loop state (resume in, final out)
+    int tiles_x, n_tiles, groups;
+    float beta;
+};
+
+// A group of consecutive blocks that reconstructs a list of slices in turn.
+struct GroupDesc {
+    int block0, nblocks;      // blocks [block0, block0 + nblocks)
+    int slice0, nslices;      // slices [slice0, slice0 + nslices) of the slice array
+    unsigned int *count;      // the group's barrier counter (own 128-byte line)
+    double *partials;         // [nblocks] FP64 partial sums of Phi
+};
+
+struct LoopArgs {
+    SliceDesc one;            // one-slice launches: the slice
+    GroupDesc one_group;      // one-slice launches: all blocks
+    const SliceDesc *slices;  // batch launches
+    const GroupDesc *groups;
+    const int *block_group;   // [grid] group of each block
+    Barrier *gbar;            // err (any wait gave up) and data_err (set-up input check)
+    unsigned long long *phase_ns; // [2] block 0's time in the two phases (first slice)
+    int n_iter;
+    double lambda0, dup, ddown, lmin, kappa;
+    float eps;
+    unsigned long long timeout_ns, spin_cap;
+    int debug_unreachable;
+};
+
+} // namespace mvct
+
 struct mvct_plan_s {
     mvct_geometry g;
     int device = 0;
@@ -36,6 +85,11 @@ struct mvct_plan_s {
     mvct::Barrier *bar = nullptr;
     unsigned long long *phase_ns = nullptr; // [2] loop phase timers
     void *loop_state = nullptr; // device copy of the resume state
+    mvct::SliceDesc *d_slice = nullptr; // the one-slice launch description
+    mvct::GroupDesc *d_group = nullptr;
+    int *d_block_group = nullptr;       // [recon_grid] zeros
+    unsigned int *d_count = nullptr;    // group barrier counter
+    bool in_batch = false;              // owned by a batch (its scratch is in use there)
     double *hist = nullptr;     // [2*hist_cap] phi and lambda per sub-iteration
     double *sched = nullptr;    // [hist_cap] lambda schedule
     int hist_cap = 0;
@@ -74,7 +128,10 @@ inline float *pad_row0(float *buf, int n) { return buf + (size_t)kPadRows * n; }
 inline size_t pad_floats(int n) { return (size_t)(n + 2 * kPadRows) * n; }
 
 // Persistent loop (mvct_recon.cu).
+// Largest persistent grid (8 co-resident blocks on each of up to 160 SMs).
+#define MVCT_MAX_RECON_GRID 1280
 int recon_occupancy(mvct_plan_s *P);
+int slice_groups(const mvct_plan_s *P, int nblocks); // view groups per tile for a group of nblocks
 
 } // namespace mvct
 

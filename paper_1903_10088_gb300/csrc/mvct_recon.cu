@@ -1,72 +1,46 @@
-// The ordered-subset TV loop as one persistent cooperative kernel.
+// The ordered-subset TV loop as one persistent cooperative kernel, for one
+// slice (mvct_recon) or many slices of uneven geometry at once (mvct_batch_*).
 //
-// Per sub-iteration n (subset s = n mod S; Eq. 3-5, Sec. 3.3.2, 3.4, 4.2):
+// The grid is partitioned into block groups; each group reconstructs its own
+// list of slices with group-local barriers (one slice: one group of all blocks).
+// Per sub-iteration n of a slice (subset s = n mod S; Eq. 3-5, Sec. 3.3.2, 3.4,
+// 4.2):
 //   phase F  one warp per ray of the subset: Joseph reprojection of mu^(n),
 //            residual r = q - p, prescaled weighted residual e = scale*w*r,
 //            FP64 partial sums of r^2 per block
 //   barrier
-//   lambda   every block reduces the partials in the same fixed order, so every
-//            block derives the same Phi_n, lambda_n (Eq. 4-5) and best-iterate
-//            decision without another barrier
-//   phase B  one thread per pixel (warps own 8x4 pixel patches): gathered
-//            matched backprojection of e, TV_eps gradient, surrogate-
-//            preconditioned step, clamp at 0, write mu^(n+1) and its transpose
+//   lambda   every block of the group reduces the partials in the same fixed
+//            order, so every block derives the same Phi_n, lambda_n (Eq. 4-5)
+//            and best-iterate decision without another barrier
+//   phase B  32x32 pixel tiles: splat of the matched backprojection of e (view
+//            groups of one tile merged in group order), TV_eps gradient,
+//            surrogate-preconditioned step, clamp at 0, write mu^(n+1) and its
+//            transpose
 //   barrier
-// The image ping-pongs between the caller's buffer and a plan buffer; the
-// transpose copy lets y-driven rays read contiguous memory.
+// Images ping-pong between two zero-row-padded plan buffers; the transposes let
+// y-driven rays read contiguous memory.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <numeric>
 #include <vector>
 
 #include "mvct_plan.h"
 
 namespace mvct {
 
-// Largest persistent grid (8 co-resident blocks on each of up to 160 SMs).
-#define MVCT_MAX_RECON_GRID 1280
-
-struct ReconArgs {
-    Geo g;
-    const float4 *rays;
-    const float4 *views;
-    const float *p;
-    const float *w;
-    const float *D;
-    float *mu0, *mu1;   // image ping-pong: sub-iteration it reads mu[it & 1]
-    float *muT0, *muT1; // and their transposes
-    float4 *e4;         // [Vs*C] (u_c, m, prescaled residual, flag) of the subset's rays
-    double *partials;
-    float *tile_part;   // [T][H-1][1024] partial tiles of the non-owner view groups
-    unsigned int *tile_flag; // [T][H-1] sub-iteration stamp of each published partial
-    float *best;
-    double *phi_hist;
-    double *lam_hist;
-    const double *sched;
-    mvct_recon_state *st;
-    Barrier *bar;
-    unsigned long long *phase_ns; // [2] block 0's time in phase F (+ barrier 1) and phase B (+ barrier 2)
-    long long n0;
-    int n_iter;
-    int tiles_x, n_tiles, groups; // phase B: 32x32 tiles x view groups
-    double lambda0, dup, ddown, lmin, kappa;
-    float beta, eps;
-    unsigned long long timeout_ns, spin_cap;
-    int debug_unreachable;
-};
-
-// Wait until flag == stamp (bounded like the grid barrier). Thread 0 only.
-__device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int stamp, Barrier *bar,
+// Wait until flag == stamp (bounded like the group barrier). Thread 0 only.
+__device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int stamp, int *err,
                                           unsigned long long timeout_ns, unsigned long long spin_cap)
 {
     if (ld_acquire(flag) == stamp) return true;
     const unsigned long long t0 = global_ns();
     unsigned long long spins = 0;
     while (ld_acquire(flag) != stamp) {
-        if (*(volatile int *)&bar->err) return false;
+        if (*(volatile int *)err) return false;
         ++spins;
         if (spins > spin_cap || ((spins & 31u) == 0 && global_ns() - t0 > timeout_ns)) {
-            atomicExch(&bar->err, 1);
+            atomicExch(err, 1);
             return false;
         }
         __nanosleep(32);
@@ -74,64 +48,73 @@ __device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
+// Shared state of one block of the loop kernel.
+struct LoopShared {
+    double ring[MVCT_MAX_SUBSETS]; // last S values of Phi of the current slice
+    double warp[kWarps];
+    double lambda, phi_prev, best_pass;
+    long long best_n;
+    float tau;
+    int best_flag, ok;
+    float acc[kWarps][kAccFloats]; // warp-private splat tiles
+    float4 stage[kWarps][32];      // warp-private ray staging
+    SliceDesc sd;                  // batch launches: the current slice
+    GroupDesc grp;                 // batch launches: this block's group
+};
+
+// All n_iter sub-iterations of one slice by the blocks of one group (lb = this
+// block's index in the group, bk = the group's barrier count so far). Returns
+// false if the block must leave the kernel (a wait gave up).
+template <class SD, class GD>
+__device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const LoopArgs &a, int lb,
+                                          unsigned int &bk, LoopShared &sh, bool timer,
+                                          unsigned long long &t_f, unsigned long long &t_b,
+                                          unsigned long long &t_mark)
 {
-    __shared__ double s_ring[MVCT_MAX_SUBSETS];
-    __shared__ double s_warp[kWarps];
-    __shared__ double s_lambda, s_phi_prev, s_best_pass;
-    __shared__ long long s_best_n;
-    __shared__ float s_tau;
-    __shared__ int s_best_flag, s_ok;
-    __shared__ float s_acc[kWarps][kAccFloats];
-    __shared__ float4 s_stage[kWarps][32];
-
-    const Geo g = a.g;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned int G = gridDim.x;
-    const int gw0 = blockIdx.x * kWarps + warp;
-    const int GW = (int)G * kWarps;
-
-    // Set-up flagged bad input: every block sees the same flag and leaves.
-    if (*(volatile int *)&a.bar->data_err) return;
-
-    for (int k = threadIdx.x; k < g.S; k += kThreads) s_ring[k] = a.st->phi_ring[k];
+    int *err = &a.gbar->err;
+    const Geo &g = sd.g;
+    mvct_recon_state *st = sd.st;
+    for (int k = threadIdx.x; k < g.S; k += kThreads) sh.ring[k] = st->phi_ring[k];
     if (threadIdx.x == 0) {
-        s_lambda = a.st->lambda;
-        s_phi_prev = a.st->phi_prev;
-        s_best_pass = a.st->best_pass;
-        s_best_n = a.st->best_n;
+        sh.lambda = st->lambda;
+        sh.phi_prev = st->phi_prev;
+        sh.best_pass = st->best_pass;
+        sh.best_n = st->best_n;
     }
     __syncthreads();
-
+    const long long n0 = st->n_done;
     const int Rs = g.Vs * g.C;
     const float S_f = (float)g.S;
-    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-    unsigned long long t_f = 0, t_b = 0, t_mark = timer ? global_ns() : 0;
+    const float4 *rays = sd.rays;
+    const float *pp = sd.p, *ww = sd.w;
+    float4 *e4 = sd.e4;
+    
 
     for (int it = 0; it < a.n_iter; ++it) {
-        const long long n = a.n0 + it;
+        const long long n = n0 + it;
         const int s = (int)(n % g.S);
         const bool odd = (it & 1) != 0;
-        const float *cur = odd ? a.mu1 : a.mu0;
-        const float *curT = odd ? a.muT1 : a.muT0;
-        float *nxt = odd ? a.mu0 : a.mu1;
-        float *nxtT = odd ? a.muT0 : a.muT1;
+        const float *cur = odd ? sd.mu1 : sd.mu0;
+        const float *curT = odd ? sd.muT1 : sd.muT0;
+        float *nxt = odd ? sd.mu0 : sd.mu1;
+        float *nxtT = odd ? sd.muT0 : sd.muT1;
         const unsigned int stamp = (unsigned int)it + 1u;
 
-        // ---- phase F: reprojection, residual, square difference -------------
+        // ---- phase F: reprojection, residual, square difference ---------
         double acc_phi = 0.0;
         {
+            const int gw0 = lb * kWarps + warp, GW = grp.nblocks * kWarps;
             // the next ray's table entry and data are fetched while this ray is walked
             float4 r_nx = make_float4(0.f, 0.f, 0.f, 1.f);
             float p_nx = 0.f, w_nx = 0.f;
-            size_t rv_nx = 0;
             if (gw0 < Rs) {
                 const int k = gw0 / g.C;
-                rv_nx = (size_t)(s + k * g.S) * g.C + (gw0 - k * g.C);
-                r_nx = __ldg(&a.rays[rv_nx]);
+                const size_t rv = (size_t)(s + k * g.S) * g.C + (gw0 - k * g.C);
+                r_nx = __ldg(&rays[rv]);
                 if (lane == 0) {
-                    p_nx = __ldg(a.p + rv_nx);
-                    w_nx = __ldg(a.w + rv_nx);
+                    p_nx = __ldg(pp + rv);
+                    w_nx = __ldg(ww + rv);
                 }
             }
             for (int ray = gw0; ray < Rs; ray += GW) {
@@ -140,180 +123,178 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
                 const int nray = ray + GW;
                 if (nray < Rs) {
                     const int k = nray / g.C;
-                    rv_nx = (size_t)(s + k * g.S) * g.C + (nray - k * g.C);
-                    r_nx = __ldg(&a.rays[rv_nx]);
+                    const size_t rv = (size_t)(s + k * g.S) * g.C + (nray - k * g.C);
+                    r_nx = __ldg(&rays[rv]);
                     if (lane == 0) {
-                        p_nx = __ldg(a.p + rv_nx);
-                        w_nx = __ldg(a.w + rv_nx);
+                        p_nx = __ldg(pp + rv);
+                        w_nx = __ldg(ww + rv);
                     }
                 }
                 const float q_ray = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
                 if (lane == 0) {
                     const float res = q_ray - pv;
-                    a.e4[ray] = make_float4(r.x, r.y, r.z * wv * res, r.w);
+                    e4[ray] = make_float4(r.x, r.y, r.z * wv * res, r.w);
                     acc_phi += (double)res * (double)res;
                 }
             }
         }
-        if (lane == 0) s_warp[warp] = acc_phi;
+        if (lane == 0) sh.warp[warp] = acc_phi;
         __syncthreads();
         if (threadIdx.x == 0) {
             double t = 0.0;
-            for (int k = 0; k < kWarps; ++k) t += s_warp[k];
-            a.partials[blockIdx.x] = t;
+            for (int k = 0; k < kWarps; ++k) t += sh.warp[k];
+            grp.partials[lb] = t;
         }
-        if (!grid_sync(a.bar, 2u * it, (it == 0 && a.debug_unreachable) ? 1u : 0u, a.timeout_ns,
-                       a.spin_cap))
-            return;
+        if (!group_sync(grp.count, err, bk, grp.nblocks, (bk == 0 && a.debug_unreachable) ? 1u : 0u,
+                        a.timeout_ns, a.spin_cap))
+            return false;
+        ++bk;
         if (timer) {
             const unsigned long long now = global_ns();
             t_f += now - t_mark;
             t_mark = now;
         }
 
-        // ---- adaptive lambda (Eq. 4-5) and best iterate (Sec. 4.2) ----------
-        // Every block sums the G partials in the same fixed order: each thread
-        // its strided share, then the warp trees, then the warps in order.
+        // ---- adaptive lambda (Eq. 4-5) and best iterate (Sec. 4.2) ------
+        // Every block sums the group's partials in the same fixed order.
         {
-            // all loads first (one round trip), then the fixed-order sums
             constexpr int L = (MVCT_MAX_RECON_GRID + kThreads - 1) / kThreads;
             double v[L];
 #pragma unroll
             for (int u = 0; u < L; ++u) {
                 const unsigned int b = threadIdx.x + u * kThreads;
-                v[u] = b < G ? a.partials[b] : 0.0;
+                v[u] = b < (unsigned int)grp.nblocks ? grp.partials[b] : 0.0;
             }
             double t = 0.0;
 #pragma unroll
             for (int u = 0; u < L; ++u) t += v[u];
             t = warp_sum(t);
-            if (lane == 0) s_warp[warp] = t;
+            if (lane == 0) sh.warp[warp] = t;
         }
         __syncthreads();
         if (warp == 0) {
             double phi = 0.0;
-            for (int k = 0; k < kWarps; ++k) phi += s_warp[k];
+            for (int k = 0; k < kWarps; ++k) phi += sh.warp[k];
             const int slot_n = (int)(n % g.S);
-            if (lane == 0) s_ring[slot_n] = phi;
+            if (lane == 0) sh.ring[slot_n] = phi;
             __syncwarp();
             // pass sum Phi_{n-S+1} + ... + Phi_n: lane-strided, then the warp tree
             double pass = 0.0;
             const bool full = n >= g.S - 1;
             if (full)
-                for (int k = lane; k < g.S; k += 32) pass += s_ring[k];
+                for (int k = lane; k < g.S; k += 32) pass += sh.ring[k];
             pass = warp_sum(pass);
             if (lane == 0) {
                 double lam;
-                if (a.sched) {
-                    lam = a.sched[it];
+                if (sd.sched) {
+                    lam = sd.sched[it];
                 } else if (n == 0) {
                     lam = a.lambda0;
                 } else {
-                    lam = s_lambda;
-                    if (phi < s_phi_prev) lam += a.dup;
-                    else if (phi > s_phi_prev) lam -= a.ddown;
+                    lam = sh.lambda;
+                    if (phi < sh.phi_prev) lam += a.dup;
+                    else if (phi > sh.phi_prev) lam -= a.ddown;
                     if (lam < a.lmin) lam = a.lmin;
                 }
-                s_lambda = lam;
-                s_phi_prev = phi;
+                sh.lambda = lam;
+                sh.phi_prev = phi;
                 int bf = 0;
-                if (full && pass < s_best_pass) {
-                    s_best_pass = pass;
-                    s_best_n = n;
+                if (full && pass < sh.best_pass) {
+                    sh.best_pass = pass;
+                    sh.best_n = n;
                     bf = 1;
                 }
-                s_best_flag = bf;
-                s_tau = (float)(a.kappa * lam);
-                if (blockIdx.x == 0) {
-                    a.phi_hist[it] = phi;
-                    a.lam_hist[it] = lam;
+                sh.best_flag = bf;
+                sh.tau = (float)(a.kappa * lam);
+                if (lb == 0) {
+                    sd.phi_hist[it] = phi;
+                    sd.lam_hist[it] = lam;
                 }
             }
         }
         __syncthreads();
 
-        // ---- phase B: tile splat (estimation) + TV + preconditioned step ----
+        // ---- phase B: tile splat (estimation) + TV + preconditioned step
         // Items: (tile t, view group h), group h holding the subset rows
         // h, h + H, h + 2H, ... Groups h < H-1 publish a partial tile; group
-        // H-1 (the owner) adds the partials in group order and updates the tile.
-        // Non-owner items come first in every block's sequence, so an owner only
-        // ever waits on items that never wait.
-        const float tau = s_tau;
-        const bool keep_best = s_best_flag && a.best;
-        const int H = a.groups;
-        const int n_items = a.n_tiles * H, n_nonowner = a.n_tiles * (H - 1);
-        const float4 *e4 = a.e4;
+        // H-1 (the owner) adds the partials in group order and updates the
+        // tile. Non-owner items come first in every block's sequence, so an
+        // owner only ever waits on items that never wait.
+        const float tau = sh.tau;
+        float *best = sd.best;
+        const bool keep_best = sh.best_flag && best;
+        const int H = sd.groups;
+        const int n_items = sd.n_tiles * H, n_nonowner = sd.n_tiles * (H - 1);
         const int C = g.C;
-        for (int item = blockIdx.x; item < n_items; item += G) {
+        const float beta = sd.beta;
+        for (int item = lb; item < n_items; item += grp.nblocks) {
             const bool owner = item >= n_nonowner;
-            const int t = owner ? item - n_nonowner : item % a.n_tiles;
-            const int h = owner ? H - 1 : item / a.n_tiles;
-            const int i_lo = (t / a.tiles_x) * kTile, j_lo = (t % a.tiles_x) * kTile;
-            const int wpos = splat_views(g, a.views, s, h, g.Vs, H, i_lo, j_lo, s_acc, s_stage,
+            const int t = owner ? item - n_nonowner : item % sd.n_tiles;
+            const int h = owner ? H - 1 : item / sd.n_tiles;
+            const int i_lo = (t / sd.tiles_x) * kTile, j_lo = (t % sd.tiles_x) * kTile;
+            const int wpos = splat_views(g, sd.views, s, h, g.Vs, H, i_lo, j_lo, sh.acc, sh.stage,
                                          [e4, C](int k, int) { return StageE4{e4 + (size_t)k * C}; });
             float part_val[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) part_val[u] = tile_sum(s_acc, threadIdx.x + u * kThreads, kWarps, wpos);
+            for (int u = 0; u < 4; ++u) part_val[u] = tile_sum(sh.acc, threadIdx.x + u * kThreads, kWarps, wpos);
 
             if (!owner) {
                 const size_t slot = (size_t)t * (H - 1) + h;
-                float *dst = a.tile_part + slot * (kTile * kTile);
+                float *dst = sd.tile_part + slot * (kTile * kTile);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) __stcg(dst + threadIdx.x + u * kThreads, part_val[u]);
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     __threadfence();
-                    st_release(a.tile_flag + slot, stamp);
+                    st_release(sd.tile_flag + slot, stamp);
                 }
-                __syncthreads(); // s_acc is zeroed by the next item
+                __syncthreads(); // sh.acc is zeroed by the next item
                 continue;
             }
 
             if (threadIdx.x == 0) {
                 bool ok = true;
                 for (int hh = 0; hh < H - 1 && ok; ++hh)
-                    ok = wait_flag(a.tile_flag + (size_t)t * (H - 1) + hh, stamp, a.bar, a.timeout_ns,
+                    ok = wait_flag(sd.tile_flag + (size_t)t * (H - 1) + hh, stamp, err, a.timeout_ns,
                                    a.spin_cap);
-                s_ok = ok;
+                sh.ok = ok;
             }
             __syncthreads();
-            if (!s_ok) return;
+            if (!sh.ok) return false;
 
-            // partial tiles of groups 0..H-2: all loads first, then the sums in group order
-            float prev[kMaxGroups - 1][4];
+            // partial tiles of groups 0..H-2, added in group order (four pixels' loads
+            // in flight per group)
+            float gsum[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int hh = 0; hh < H - 1; ++hh) {
+                const float *src = sd.tile_part + ((size_t)t * (H - 1) + hh) * (kTile * kTile) + threadIdx.x;
+                float v[4];
 #pragma unroll
-            for (int hh = 0; hh < kMaxGroups - 1; ++hh)
+                for (int u = 0; u < 4; ++u) v[u] = __ldcg(src + u * kThreads);
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    prev[hh][u] = hh < H - 1 ? __ldcg(a.tile_part + ((size_t)t * (H - 1) + hh) * (kTile * kTile) +
-                                                      threadIdx.x + u * kThreads)
-                                             : 0.f;
-            float *tile = s_acc[0]; // reused for the transposed write-out
+                for (int u = 0; u < 4; ++u) gsum[u] += v[u];
+            }
+            float *tile = sh.acc[0]; // reused for the transposed write-out
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int idx = threadIdx.x + u * kThreads;
                 const int ii = idx >> 5, jj = idx & 31;
-                float gs = 0.f;
-#pragma unroll
-                for (int hh = 0; hh < kMaxGroups - 1; ++hh)
-                    if (hh < H - 1) gs += prev[hh][u];
-                gs += part_val[u];
+                const float gs = gsum[u] + part_val[u];
                 const int i = i_lo + ii, j = j_lo + jj;
                 float nm = 0.f;
                 if (i < g.n && j < g.n) {
                     const size_t r = (size_t)i * g.n + j;
                     const float m = cur[r];
-                    const float d = __ldg(a.D + r);
-                    if (keep_best) a.best[r] = m;
+                    const float d = __ldg(sd.D + r);
+                    if (keep_best) best[r] = m;
                     if (d > 0.f) {
                         const float tg = tv_grad_pixel<false>(cur, g.n, i, j, a.eps, nullptr);
-                        nm = fmaxf(0.f, m - tau * d * fmaf(S_f, gs, a.beta * tg));
+                        nm = fmaxf(0.f, m - tau * d * fmaf(S_f, gs, beta * tg));
                     }
                     nxt[r] = nm;
                 }
                 part_val[u] = nm;
             }
-            __syncthreads(); // every warp has finished reading s_acc
+            __syncthreads(); // every warp has finished reading sh.acc
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int idx = threadIdx.x + u * kThreads;
@@ -327,9 +308,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
                 const int i = i_lo + ii, j = j_lo + jj;
                 if (i < g.n && j < g.n) nxtT[(size_t)j * g.n + i] = tile[ii * kAccStride + jj];
             }
-            __syncthreads(); // tile (s_acc[0]) is zeroed by the next item
+            __syncthreads(); // tile (sh.acc[0]) is zeroed by the next item
         }
-        if (!grid_sync(a.bar, 2u * it + 1u, 0u, a.timeout_ns, a.spin_cap)) return;
+        if (!group_sync(grp.count, err, bk, grp.nblocks, 0u, a.timeout_ns, a.spin_cap)) return false;
+        ++bk;
         if (timer) {
             const unsigned long long now = global_ns();
             t_b += now - t_mark;
@@ -337,18 +319,65 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
         }
     }
 
+    if (lb == 0) {
+        for (int k = threadIdx.x; k < g.S; k += kThreads) st->phi_ring[k] = sh.ring[k];
+        if (threadIdx.x == 0) {
+            st->n_done = n0 + a.n_iter;
+            st->lambda = sh.lambda;
+            st->phi_prev = sh.phi_prev;
+            st->best_pass = sh.best_pass;
+            st->best_n = sh.best_n;
+        }
+    }
+    __syncthreads(); // the next slice re-initialises the shared state
+    return true;
+}
+
+// The loop kernel: BATCH = false reads the one slice and group from the kernel
+// parameters; BATCH = true reads each block's group and its slices from global
+// descriptor arrays (copied to shared memory).
+template <bool BATCH>
+__global__ void __launch_bounds__(kThreads, 4) k_recon(LoopArgs a)
+{
+    __shared__ LoopShared sh;
+    // Set-up flagged bad input: every block sees the same flag and leaves.
+    if (*(volatile int *)&a.gbar->data_err) return;
+    unsigned int bk = 0; // group barriers passed
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_f = 0, t_b = 0, t_mark = timer ? global_ns() : 0;
+    if constexpr (BATCH) {
+        if (threadIdx.x == 0) sh.grp = a.groups[a.block_group[blockIdx.x]];
+        __syncthreads();
+        const int lb = blockIdx.x - sh.grp.block0;
+        for (int si = 0; si < sh.grp.nslices; ++si) {
+            {
+                const int *src = (const int *)(a.slices + sh.grp.slice0 + si);
+                int *dst = (int *)&sh.sd;
+                for (int k = threadIdx.x; k < (int)(sizeof(SliceDesc) / sizeof(int)); k += kThreads) dst[k] = src[k];
+            }
+            __syncthreads();
+            if (!run_slice(sh.sd, sh.grp, a, lb, bk, sh, timer && si == 0, t_f, t_b, t_mark)) return;
+        }
+    } else {
+        if (!run_slice(a.one, a.one_group, a, (int)blockIdx.x, bk, sh, timer, t_f, t_b, t_mark)) return;
+    }
     if (timer) {
         a.phase_ns[0] = t_f;
         a.phase_ns[1] = t_b;
     }
-    if (blockIdx.x == 0) {
-        for (int k = threadIdx.x; k < g.S; k += kThreads) a.st->phi_ring[k] = s_ring[k];
+}
+
+// Fresh loop state for `count` slices.
+__global__ void k_state_init(mvct_recon_state *st, int count, double lambda0)
+{
+    for (int b = blockIdx.x; b < count; b += gridDim.x) {
+        for (int k = threadIdx.x; k < MVCT_MAX_SUBSETS; k += blockDim.x) st[b].phi_ring[k] = 0.0;
         if (threadIdx.x == 0) {
-            a.st->n_done = a.n0 + a.n_iter;
-            a.st->lambda = s_lambda;
-            a.st->phi_prev = s_phi_prev;
-            a.st->best_pass = s_best_pass;
-            a.st->best_n = s_best_n;
+            st[b].n_done = 0;
+            st[b].lambda = lambda0;
+            st[b].phi_prev = 0.0;
+            st[b].best_pass = INFINITY;
+            st[b].best_n = -1;
         }
     }
 }
@@ -356,9 +385,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(ReconArgs a)
 int recon_occupancy(mvct_plan_s *P)
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_recon, kThreads, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_recon<false>, kThreads, 0) != cudaSuccess)
         return 0;
     return std::min(nb * P->num_sms, MVCT_MAX_RECON_GRID);
+}
+
+int slice_groups(const mvct_plan_s *P, int nblocks)
+{
+    return std::max(1, std::min(P->groups, nblocks / P->n_tiles));
 }
 
 } // namespace mvct
@@ -435,6 +469,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         return mvct_fail(MVCT_EINVAL, "mvct_recon: resuming (state->n_done > 0) needs init_from_input = 1");
     if (P->recon_grid <= 0) return mvct_fail(MVCT_ELAUNCH, "mvct_recon: loop kernel has no occupancy");
 
+    if (P->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_recon: plan belongs to a batch");
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
     const Geo &g = P->geo;
@@ -461,19 +496,47 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         hs.best_pass = INFINITY;
         hs.best_n = -1;
     }
+    const int n = g.n;
+    float *mu_a = pad_row0(P->pad[0], n), *mu_b = pad_row0(P->pad[1], n);
+    float *muT_a = pad_row0(P->pad[2], n), *muT_b = pad_row0(P->pad[3], n);
+
+    SliceDesc sd;
+    std::memset(&sd, 0, sizeof(sd));
+    sd.g = g;
+    sd.rays = P->rays;
+    sd.views = P->views;
+    sd.p = d_sino;
+    sd.w = d_weights;
+    sd.D = P->D;
+    sd.mu0 = mu_a;
+    sd.mu1 = mu_b;
+    sd.muT0 = muT_a;
+    sd.muT1 = muT_b;
+    sd.e4 = P->e4;
+    sd.tile_part = P->tile_part;
+    sd.tile_flag = P->tile_flag;
+    sd.best = o.d_best_out;
+    sd.phi_hist = P->hist;
+    sd.lam_hist = P->hist + n_iter;
+    sd.sched = o.lambda_schedule ? P->sched : nullptr;
+    sd.st = (mvct_recon_state *)P->loop_state;
+    sd.tiles_x = P->tiles_x;
+    sd.n_tiles = P->n_tiles;
+    sd.groups = slice_groups(P, P->recon_grid);
+    sd.beta = (float)beta;
+    GroupDesc gd{0, P->recon_grid, 0, 1, P->d_count, P->partials};
+
     CK(cudaMemcpyAsync(P->loop_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     if (o.lambda_schedule && n_iter > 0)
         CK(cudaMemcpyAsync(P->sched, o.lambda_schedule, sizeof(double) * n_iter, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
+    CK(cudaMemsetAsync(P->d_count, 0, 128, st));
     CK(cudaMemsetAsync(P->phase_ns, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups, st));
 
     Events ev;
     CK(cudaEventRecord(ev.e[0], st));
     // set-up (a0): w .* A1 over all views (and input validation), then D and mu0
-    const int n = g.n;
-    float *mu_a = pad_row0(P->pad[0], n), *mu_b = pad_row0(P->pad[1], n);
-    float *muT_a = pad_row0(P->pad[2], n), *muT_b = pad_row0(P->pad[3], n);
     const float *ones = pad_row0(P->pad_ones, n);
     CK(launch_forward(P, ones, ones, P->sino_tmp, -1, d_weights, d_sino, &P->bar->data_err, st));
     const double cb = beta * 8.0 / std::sqrt(o.tv_eps);
@@ -482,46 +545,24 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     CK(cudaEventRecord(ev.e[1], st));
 
     if (n_iter > 0) {
-        ReconArgs a;
+        LoopArgs a;
         std::memset(&a, 0, sizeof(a));
-        a.g = g;
-        a.rays = P->rays;
-        a.views = P->views;
-        a.p = d_sino;
-        a.w = d_weights;
-        a.D = P->D;
-        a.mu0 = mu_a;
-        a.mu1 = mu_b;
-        a.muT0 = muT_a;
-        a.muT1 = muT_b;
-        a.e4 = P->e4;
-        a.partials = P->partials;
-        a.tile_part = P->tile_part;
-        a.tile_flag = P->tile_flag;
-        a.tiles_x = P->tiles_x;
-        a.n_tiles = P->n_tiles;
-        a.groups = P->groups;
-        a.best = o.d_best_out;
-        a.phi_hist = P->hist;
-        a.lam_hist = P->hist + n_iter;
-        a.sched = o.lambda_schedule ? P->sched : nullptr;
-        a.st = (mvct_recon_state *)P->loop_state;
-        a.bar = P->bar;
+        a.one = sd;
+        a.one_group = gd;
+        a.gbar = P->bar;
         a.phase_ns = P->phase_ns;
-        a.n0 = hs.n_done;
         a.n_iter = n_iter;
         a.lambda0 = o.lambda0;
         a.dup = o.dlambda_up;
         a.ddown = o.dlambda_down;
         a.lmin = o.lambda_min;
         a.kappa = o.kappa;
-        a.beta = (float)beta;
         a.eps = (float)o.tv_eps;
         a.timeout_ns = (unsigned long long)(o.barrier_timeout_ms * 1e6);
         a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
         void *args[] = {&a};
-        cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon, dim3(P->recon_grid),
+        cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon<false>, dim3(P->recon_grid),
                                                      dim3(kThreads), args, 0, st);
         if (le == cudaErrorCooperativeLaunchTooLarge)
             return mvct_fail(MVCT_ELAUNCH, "mvct_recon: %d blocks cannot be co-resident", P->recon_grid);
@@ -563,5 +604,338 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         stats->grid_blocks = P->recon_grid;
         stats->block_threads = kThreads;
     }
+    return MVCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many slices of uneven geometry in one persistent launch.
+// ---------------------------------------------------------------------------
+struct mvct_batch_s {
+    int device = 0, count = 0, grid = 0, ngroups = 0, max_iter = 0;
+    std::vector<mvct_plan_s *> plans;   // user order
+    std::vector<int> pos;               // user slice -> position in the descriptor array
+    std::vector<int> group_blocks;      // blocks of the group of each user slice
+    SliceDesc *d_slices = nullptr;
+    GroupDesc *d_groups = nullptr;
+    int *d_block_group = nullptr;
+    unsigned int *d_counts = nullptr;   // [ngroups][32]
+    double *d_partials = nullptr;       // [grid]
+    Barrier *d_bar = nullptr;
+    unsigned long long *d_phase = nullptr;
+    mvct_recon_state *d_states = nullptr; // [count] in descriptor order
+    double *d_hist = nullptr;           // [count][2][max_iter] in descriptor order
+    std::vector<float *> imgs;          // user order
+    std::vector<const float *> sinos, weights;
+    std::vector<double> betas;
+    mvct_recon_opts opts;
+    bool bound = false;
+    int last_n_iter = 0;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+void free_batch(mvct_batch_s *b)
+{
+    if (!b) return;
+    void *ptrs[] = {b->d_slices, b->d_groups, b->d_block_group, b->d_counts, b->d_partials,
+                    b->d_bar, b->d_phase, b->d_states, b->d_hist};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (auto &e : b->ev)
+        if (e) cudaEventDestroy(e);
+    for (auto *p : b->plans)
+        if (p) p->in_batch = false;
+    delete b;
+}
+
+double slice_work(const mvct_plan_s *P)
+{
+    // both loop phases scale with the rays of a subset times the image side
+    return (double)P->geo.Vs * P->geo.C * P->geo.n;
+}
+
+} // namespace
+
+extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_batch *out)
+{
+    if (!out) return mvct_fail(MVCT_EINVAL, "mvct_batch_create: out is NULL");
+    *out = nullptr;
+    if (!plans || count < 1) return mvct_fail(MVCT_EINVAL, "mvct_batch_create: need at least one plan");
+    for (int i = 0; i < count; ++i) {
+        if (!plans[i]) return mvct_fail(MVCT_EINVAL, "mvct_batch_create: plan %d is NULL", i);
+        if (plans[i]->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_batch_create: plan %d is in another batch", i);
+        if (plans[i]->device != plans[0]->device)
+            return mvct_fail(MVCT_EINVAL, "mvct_batch_create: plans on different devices");
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == plans[i]) return mvct_fail(MVCT_EINVAL, "mvct_batch_create: plan %d appears twice", i);
+    }
+    DeviceGuard dg(plans[0]->device);
+    mvct_batch_s *b = new mvct_batch_s();
+    b->device = plans[0]->device;
+    b->count = count;
+    b->grid = plans[0]->recon_grid;
+    b->plans.assign(plans, plans + count);
+    const int G = b->grid;
+    if (G <= 0) {
+        free_batch(b);
+        return mvct_fail(MVCT_ELAUNCH, "mvct_batch_create: loop kernel has no occupancy");
+    }
+
+    // Partition the grid into groups. Up to G slices: one group per slice, blocks
+    // in proportion to the slice's work (largest remainders, at least one each).
+    // More slices: G one-block groups, slices dealt longest-first to the least
+    // loaded group.
+    std::vector<double> work(count);
+    for (int i = 0; i < count; ++i) work[i] = slice_work(plans[i]);
+    std::vector<std::vector<int>> members;
+    std::vector<int> nblocks;
+    if (count <= G) {
+        const double total = std::accumulate(work.begin(), work.end(), 0.0);
+        nblocks.assign(count, 1);
+        int left = G - count;
+        std::vector<std::pair<double, int>> rem;
+        for (int i = 0; i < count; ++i) {
+            const double ideal = G * work[i] / total - 1.0;
+            const int extra = std::max(0, std::min(left, (int)std::floor(ideal)));
+            nblocks[i] += extra;
+            left -= extra;
+            rem.push_back({ideal - extra, i});
+        }
+        std::sort(rem.begin(), rem.end(), [](auto &x, auto &y) { return x.first > y.first; });
+        for (int k = 0; left > 0 && k < count; ++k, --left) nblocks[rem[k].second] += 1;
+        for (int i = 0; i < count; ++i) members.push_back({i});
+    } else {
+        std::vector<int> idx(count);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return work[x] > work[y]; });
+        members.assign(G, {});
+        std::vector<double> load(G, 0.0);
+        for (int i : idx) {
+            const int gmin = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            members[gmin].push_back(i);
+            load[gmin] += work[i];
+        }
+        nblocks.assign(G, 1);
+    }
+    b->ngroups = (int)members.size();
+    std::vector<GroupDesc> groups(b->ngroups);
+    std::vector<int> block_group(G);
+    b->pos.assign(count, 0);
+    b->group_blocks.assign(count, 1);
+    int block0 = 0, slice0 = 0;
+    for (int gi = 0; gi < b->ngroups; ++gi) {
+        groups[gi] = GroupDesc{block0, nblocks[gi], slice0, (int)members[gi].size(), nullptr, nullptr};
+        for (int k = 0; k < nblocks[gi]; ++k) block_group[block0 + k] = gi;
+        for (int i : members[gi]) {
+            b->pos[i] = slice0++;
+            b->group_blocks[i] = nblocks[gi];
+        }
+        block0 += nblocks[gi];
+    }
+    bool ok = cudaMalloc(&b->d_slices, sizeof(SliceDesc) * count) == cudaSuccess &&
+              cudaMalloc(&b->d_groups, sizeof(GroupDesc) * b->ngroups) == cudaSuccess &&
+              cudaMalloc(&b->d_block_group, sizeof(int) * G) == cudaSuccess &&
+              cudaMalloc(&b->d_counts, 128 * (size_t)b->ngroups) == cudaSuccess &&
+              cudaMalloc(&b->d_partials, sizeof(double) * G) == cudaSuccess &&
+              cudaMalloc(&b->d_bar, sizeof(Barrier)) == cudaSuccess &&
+              cudaMalloc(&b->d_phase, 2 * sizeof(unsigned long long)) == cudaSuccess &&
+              cudaMalloc(&b->d_states, sizeof(mvct_recon_state) * count) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_batch(b);
+        return mvct_fail(MVCT_ENOMEM, "mvct_batch_create: device allocation failed");
+    }
+    for (int gi = 0; gi < b->ngroups; ++gi) {
+        groups[gi].count = b->d_counts + 32 * gi;
+        groups[gi].partials = b->d_partials + groups[gi].block0;
+    }
+    cudaError_t e = cudaMemcpy(b->d_groups, groups.data(), sizeof(GroupDesc) * b->ngroups, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_block_group, block_group.data(), sizeof(int) * G, cudaMemcpyHostToDevice);
+    for (auto &ev : b->ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return mvct_fail(MVCT_ECUDA, "mvct_batch_create: %s", cudaGetErrorString(e));
+    }
+    for (auto *p : b->plans) p->in_batch = true;
+    *out = b;
+    return MVCT_OK;
+}
+
+extern "C" void mvct_batch_destroy(mvct_batch b)
+{
+    if (!b) return;
+    DeviceGuard dg(b->device);
+    cudaDeviceSynchronize();
+    free_batch(b);
+}
+
+extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const float *const *d_weights,
+                               const double *betas, float *const *d_imgs, int32_t max_iter,
+                               const mvct_recon_opts *opts_in)
+{
+    if (!b) return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: null batch");
+    if (!d_sinos || !d_weights || !betas || !d_imgs || max_iter < 0)
+        return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: null array or negative max_iter");
+    mvct_recon_opts o;
+    if (opts_in) o = *opts_in;
+    else mvct_recon_opts_init(&o);
+    if (o.lambda_schedule || o.state || o.d_best_out)
+        return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: lambda_schedule, state and d_best_out are one-slice options");
+    if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
+        !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0))
+        return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: invalid options");
+    for (int i = 0; i < b->count; ++i) {
+        if (!d_sinos[i] || !d_weights[i] || !d_imgs[i])
+            return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: null device pointer for slice %d", i);
+        if (!std::isfinite(betas[i]) || betas[i] < 0)
+            return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: beta of slice %d must be finite and >= 0", i);
+    }
+    DeviceGuard dg(b->device);
+    if (max_iter > b->max_iter || !b->d_hist) {
+        if (b->d_hist) cudaFree(b->d_hist);
+        b->d_hist = nullptr;
+        if (cudaMalloc(&b->d_hist, sizeof(double) * 2 * std::max(1, max_iter) * (size_t)b->count) != cudaSuccess)
+            return mvct_fail(MVCT_ENOMEM, "mvct_batch_bind: cannot allocate history");
+    }
+    b->max_iter = std::max(max_iter, b->max_iter);
+    std::vector<SliceDesc> h(b->count);
+    for (int i = 0; i < b->count; ++i) {
+        mvct_plan_s *P = b->plans[i];
+        const int n = P->geo.n, q = b->pos[i];
+        SliceDesc &sd = h[q];
+        std::memset(&sd, 0, sizeof(sd));
+        sd.g = P->geo;
+        sd.rays = P->rays;
+        sd.views = P->views;
+        sd.p = d_sinos[i];
+        sd.w = d_weights[i];
+        sd.D = P->D;
+        sd.mu0 = pad_row0(P->pad[0], n);
+        sd.mu1 = pad_row0(P->pad[1], n);
+        sd.muT0 = pad_row0(P->pad[2], n);
+        sd.muT1 = pad_row0(P->pad[3], n);
+        sd.e4 = P->e4;
+        sd.tile_part = P->tile_part;
+        sd.tile_flag = P->tile_flag;
+        sd.phi_hist = b->d_hist + (size_t)q * 2 * b->max_iter;
+        sd.lam_hist = sd.phi_hist + b->max_iter;
+        sd.st = b->d_states + q;
+        sd.tiles_x = P->tiles_x;
+        sd.n_tiles = P->n_tiles;
+        sd.groups = slice_groups(P, b->group_blocks[i]);
+        sd.beta = (float)betas[i];
+    }
+    cudaError_t e = cudaMemcpy(b->d_slices, h.data(), sizeof(SliceDesc) * b->count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return mvct_fail(MVCT_ECUDA, "mvct_batch_bind: %s", cudaGetErrorString(e));
+    b->imgs.assign(d_imgs, d_imgs + b->count);
+    b->sinos.assign(d_sinos, d_sinos + b->count);
+    b->weights.assign(d_weights, d_weights + b->count);
+    b->betas.assign(betas, betas + b->count);
+    b->opts = o;
+    b->bound = true;
+    return MVCT_OK;
+}
+
+extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
+{
+    if (!b || !b->bound) return mvct_fail(MVCT_EINVAL, "mvct_batch_run: batch not bound");
+    if (n_iter < 0 || n_iter > b->max_iter)
+        return mvct_fail(MVCT_EINVAL, "mvct_batch_run: n_iter %d outside 0..%d", n_iter, b->max_iter);
+    DeviceGuard dg(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const mvct_recon_opts &o = b->opts;
+    CK(cudaEventRecord(b->ev[0], st));
+    CK(cudaMemsetAsync(b->d_bar, 0, sizeof(Barrier), st));
+    CK(cudaMemsetAsync(b->d_counts, 0, 128 * (size_t)b->ngroups, st));
+    CK(cudaMemsetAsync(b->d_phase, 0, 2 * sizeof(unsigned long long), st));
+    k_state_init<<<std::min(b->count, 1024), 256, 0, st>>>(b->d_states, b->count, o.lambda0);
+    CK(cudaGetLastError());
+    // set-up of every slice (a0): w .* A1 with the input check, then D and mu0
+    for (int i = 0; i < b->count; ++i) {
+        mvct_plan_s *P = b->plans[i];
+        const int n = P->geo.n;
+        const float *ones = pad_row0(P->pad_ones, n);
+        CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups, st));
+        CK(launch_forward(P, ones, ones, P->sino_tmp, -1, b->weights[i], b->sinos[i], &b->d_bar->data_err, st));
+        const double cb = b->betas[i] * 8.0 / std::sqrt(o.tv_eps);
+        CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0, b->imgs[i],
+                             pad_row0(P->pad[0], n), pad_row0(P->pad[2], n), st));
+    }
+    CK(cudaEventRecord(b->ev[1], st));
+    if (n_iter > 0) {
+        LoopArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.slices = b->d_slices;
+        a.groups = b->d_groups;
+        a.block_group = b->d_block_group;
+        a.gbar = b->d_bar;
+        a.phase_ns = b->d_phase;
+        a.n_iter = n_iter;
+        a.lambda0 = o.lambda0;
+        a.dup = o.dlambda_up;
+        a.ddown = o.dlambda_down;
+        a.lmin = o.lambda_min;
+        a.kappa = o.kappa;
+        a.eps = (float)o.tv_eps;
+        a.timeout_ns = (unsigned long long)(o.barrier_timeout_ms * 1e6);
+        a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
+        a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
+        void *args[] = {&a};
+        cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads),
+                                                     args, 0, st);
+        if (le == cudaErrorCooperativeLaunchTooLarge)
+            return mvct_fail(MVCT_ELAUNCH, "mvct_batch_run: %d blocks cannot be co-resident", b->grid);
+        if (le != cudaSuccess)
+            return mvct_fail(MVCT_ECUDA, "mvct_batch_run: cooperative launch: %s", cudaGetErrorString(le));
+    }
+    for (int i = 0; i < b->count; ++i) {
+        mvct_plan_s *P = b->plans[i];
+        const int n = P->geo.n;
+        CK(cudaMemcpyAsync(b->imgs[i], pad_row0(P->pad[(n_iter & 1) ? 1 : 0], n), (size_t)n * n * sizeof(float),
+                           cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaEventRecord(b->ev[2], st));
+    b->last_n_iter = n_iter;
+    return MVCT_OK;
+}
+
+extern "C" int mvct_batch_stats(mvct_batch b, int32_t slice, mvct_recon_stats *stats)
+{
+    if (!b || !b->bound) return mvct_fail(MVCT_EINVAL, "mvct_batch_stats: batch not bound");
+    if (slice < 0 || slice >= b->count) return mvct_fail(MVCT_EINVAL, "mvct_batch_stats: slice %d out of range", slice);
+    DeviceGuard dg(b->device);
+    // the run may have been replayed from a CUDA graph (its event records are then
+    // graph nodes, not these events): wait for the whole device
+    CK(cudaDeviceSynchronize());
+    Barrier hb;
+    CK(cudaMemcpy(&hb, b->d_bar, sizeof(hb), cudaMemcpyDeviceToHost));
+    if (hb.data_err) return mvct_fail(MVCT_EDATA, "mvct_batch: non-finite projections/weights or negative weights");
+    if (hb.err)
+        return mvct_fail(MVCT_ETIMEOUT, "mvct_batch: group barrier wait exceeded %.1f ms", b->opts.barrier_timeout_ms);
+    if (!stats) return MVCT_OK;
+    const int q = b->pos[slice], n_iter = b->last_n_iter;
+    mvct_recon_state hs;
+    CK(cudaMemcpy(&hs, b->d_states + q, sizeof(hs), cudaMemcpyDeviceToHost));
+    if (n_iter > 0) {
+        const double *src = b->d_hist + (size_t)q * 2 * b->max_iter;
+        if (stats->phi) CK(cudaMemcpy(stats->phi, src, sizeof(double) * n_iter, cudaMemcpyDeviceToHost));
+        if (stats->lambda) CK(cudaMemcpy(stats->lambda, src + b->max_iter, sizeof(double) * n_iter, cudaMemcpyDeviceToHost));
+    }
+    stats->best_n = hs.best_n;
+    stats->best_pass = hs.best_pass;
+    float t1 = -1.f, t2 = -1.f; // -1: the last run was a graph replay (times not available)
+    if (cudaEventElapsedTime(&t1, b->ev[0], b->ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&t2, b->ev[1], b->ev[2]) != cudaSuccess) {
+        cudaGetLastError();
+        t1 = t2 = -1.f;
+    }
+    stats->setup_ms = t1;
+    stats->loop_ms = t2;
+    stats->forward_ms = 0.0;
+    stats->back_ms = 0.0;
+    stats->grid_blocks = b->group_blocks[slice];
+    stats->block_threads = kThreads;
     return MVCT_OK;
 }

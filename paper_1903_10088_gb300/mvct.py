@@ -92,7 +92,8 @@ class ReconStats(ctypes.Structure):
 
 EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
            "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error",
-           "mvct_tv_grad_noalloc"]
+           "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
+           "mvct_batch_run", "mvct_batch_stats"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -112,6 +113,13 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     lib.mvct_recon.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(ReconOpts), vp,
                                ctypes.POINTER(ReconStats), vp]
     lib.mvct_tv_grad_noalloc.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp]
+    lib.mvct_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+    lib.mvct_batch_destroy.argtypes = [vp]
+    lib.mvct_batch_destroy.restype = None
+    lib.mvct_batch_bind.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(vp), i32, ctypes.POINTER(ReconOpts)]
+    lib.mvct_batch_run.argtypes = [vp, i32, vp]
+    lib.mvct_batch_stats.argtypes = [vp, i32, ctypes.POINTER(ReconStats)]
     lib.mvct_last_error.restype = ctypes.c_char_p
     lib.mvct_last_error.argtypes = []
     return lib
@@ -278,6 +286,73 @@ def tv_grad_noalloc(img: torch.Tensor, eps: float, grad: torch.Tensor, tv: Optio
     _check(lib().mvct_tv_grad_noalloc(_dev_f32(img, n * n, "img"), n, eps, _dev_f32(grad, n * n, "grad"),
                                       ctypes.c_void_p(tv.data_ptr()) if tv is not None else None,
                                       ctypes.c_void_p(_stream(stream))))
+
+
+class Batch:
+    """Many slices in one persistent launch (``mvct_batch_*``).
+
+    ``plans``: distinct :class:`Plan` objects (one per slice). ``bind`` keeps the
+    tensors alive; ``run`` only enqueues work on the stream (CUDA-graph
+    capturable); ``stats`` waits for it.
+    """
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(lib().mvct_batch_create(arr, len(self.plans), ctypes.byref(h)))
+        self._h = h
+        self._keep = None
+        self.max_iter = 0
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().mvct_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def bind(self, sinos, weights, betas, imgs, max_iter: int, init_from_input: bool = False, **opts):
+        m = len(self.plans)
+        assert len(sinos) == len(weights) == len(betas) == len(imgs) == m
+        ptr = lambda ts, nm, sizes: (ctypes.c_void_p * m)(*[_dev_f32(t, k, nm).value for t, k in zip(ts, sizes)])
+        R = [p.V * p.C for p in self.plans]
+        N = [p.n * p.n for p in self.plans]
+        o = ReconOpts()
+        lib().mvct_recon_opts_init(ctypes.byref(o))
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError(f"unknown option {k}")
+            setattr(o, k, v)
+        o.init_from_input = 1 if init_from_input else 0
+        b = (ctypes.c_double * m)(*[float(x) for x in betas])
+        _check(lib().mvct_batch_bind(self._h, ptr(sinos, "p", R), ptr(weights, "w", R), b, ptr(imgs, "img", N),
+                                     max_iter, ctypes.byref(o)))
+        self._keep = (list(sinos), list(weights), list(imgs))
+        self.max_iter = max_iter
+
+    def run(self, n_iter: int, stream=None):
+        _check(lib().mvct_batch_run(self._h, n_iter, ctypes.c_void_p(_stream(stream))))
+
+    def stats(self, i: int, n_iter: int) -> ReconResult:
+        phi = np.zeros(max(n_iter, 1))
+        lam = np.zeros(max(n_iter, 1))
+        st = ReconStats()
+        st.phi = phi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        st.lambda_ = lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().mvct_batch_stats(self._h, i, ctypes.byref(st)))
+        return ReconResult(phi[:n_iter], lam[:n_iter], st.best_n, st.best_pass, st.loop_ms, st.setup_ms,
+                           st.grid_blocks)
 
 
 def fresh_state() -> ReconState:
