@@ -37,6 +37,10 @@ WORKLOAD = dict(workload="plain OS-TV, one 512^2 slice per step", n=512, fov_cm=
                 n_channels=738, sad_cm=85.0, subsets=20, sub_iterations=500, beta=1e-3, tv_eps=1e-6,
                 I0=5e3, phantom="water disk + 7 low-contrast inserts + 4 rods (seeded)")
 METRIC = "512^2 slices/s at 500 OS-TV iters (plain); GRay/s; %HBM"
+BATCH_WORKLOAD = dict(workload="batched uneven helical stack, 96 slices per step in one persistent launch",
+                      slices="48 x 512^2 (800 views x 738 ch) + 32 x 384^2 (600 x 552) + 16 x 256^2 (400 x 368)",
+                      fov_cm=40.0, sad_cm=85.0, subsets=20, sub_iterations=500, beta=1e-3, tv_eps=1e-6,
+                      I0="log-uniform in [2e3, 2e4] per slice", launch="CUDA-graph replay of mvct_batch_run")
 SEED0 = 100
 L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
@@ -45,7 +49,17 @@ PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # --------------------------------------------------------------------------
 # accounting
 # --------------------------------------------------------------------------
+_TAPS = {}
+
+
 def tap_counts(geom: ph.Geometry, n_subsets: int) -> np.ndarray:
+    key = (geom, n_subsets)
+    if key not in _TAPS:
+        _TAPS[key] = _tap_counts(geom, n_subsets)
+    return _TAPS[key]
+
+
+def _tap_counts(geom: ph.Geometry, n_subsets: int) -> np.ndarray:
     """In-image Joseph taps (ray, pixel pairs) of every subset: the number of
     interpolation taps the reprojection reads, equal to the number of
     residual reads of the matched backprojection. Pure geometry accounting."""
@@ -357,6 +371,113 @@ def run_ours(args):
     return 0
 
 
+def _make_batch_case(args):
+    seed, n, V, C, I0 = args
+    g = ph.Geometry(n=n, n_views=V, n_channels=C)
+    return ph.make_case("full", seed, geom=g, I0=I0)
+
+
+def batch_cases(seed0=1000, groups=ph.BATCH_GROUPS, workers=8):
+    """The 96-slice uneven stack, generated in spawned worker processes."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    jobs = []
+    k = 0
+    for count, g in groups:
+        for _ in range(count):
+            rng = np.random.Generator(np.random.PCG64(seed0 + k))
+            I0 = float(math.exp(rng.uniform(math.log(2e3), math.log(2e4))))
+            jobs.append((seed0 + k, g.n, g.n_views, g.n_channels, I0))
+            k += 1
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_make_batch_case, jobs))
+
+
+def run_batched(args):
+    """Batched workload: all slices of the stack reconstructed per step."""
+    cases = batch_cases()
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1903_10088_gb300 import mvct
+
+    mvct.lib()
+    n_iter = cases[0].n_iter
+    plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
+    p = [torch.from_numpy(c.p).to(dev) for c in cases]
+    w = [torch.from_numpy(c.w).to(dev) for c in cases]
+    imgs = [torch.zeros((c.geom.n, c.geom.n), device=dev) for c in cases]
+    batch = mvct.Batch(plans)
+    batch.bind(p, w, [c.beta for c in cases], imgs, n_iter)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    batch.run(n_iter, stream=s)                       # first call outside capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            batch.run(n_iter, stream=s)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    batch.stats(0, n_iter)                            # raises if the runs failed
+    cur = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(cur)
+            graph.replay()
+            ev[k][1].record(cur)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_max = max_over_ranks(float(np.sum(step_ms)), dev)
+    n_slices = len(cases) * ws * args.steps
+    value = n_slices / (t_max / 1e3)
+    work = [c.geom.n_views / c.n_subsets * c.geom.n_channels * c.geom.n for c in cases]
+    w512 = 800 / 20 * 738 * 512
+    equiv = sum(work) / w512 * ws * args.steps / (t_max / 1e3)
+    taps = [tap_counts(c.geom, c.n_subsets) for c in cases]
+    tap_total = sum(float(sum(t[n % c.n_subsets] for n in range(n_iter))) for t, c in zip(taps, cases))
+    peaks, peak_kind = load_peaks()
+    achieved = 2 * 4 * tap_total / (np.mean(step_ms) / 1e3) / 1e9
+    line = {
+        "metric": "slices/s of the batched uneven stack at 500 OS-TV iters (plain start)", "value": value,
+        "unit": "slices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": dict(BATCH_WORKLOAD, l2="flushed between timed steps (512 MiB write)",
+                       parallelism=f"replicas x{ws}, one stack per GPU per step"),
+        "slices_512_equivalent_per_s": equiv,
+        "gray_per_s": 2.0 * tap_total / (np.mean(step_ms) / 1e3) / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "k_recon<batch> + set-up (whole graph)",
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "clocks": clk.summary(),
+        "gpu_launches": (1 + 3 * len(cases)) * args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    batch.close()
+    for pl in plans:
+        pl.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -366,9 +487,12 @@ def main(argv=None):
     ap.add_argument("--ref-sub-iters", type=int, default=40,
                     help="oracle sub-iterations timed per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["plain", "batched"], default="plain")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -92,7 +92,16 @@ typedef struct mvct_recon_opts {
     mvct_recon_state *state;       /* host in/out resume state, or NULL */
     double barrier_timeout_ms;     /* grid-barrier wait limit (2000) */
     int32_t debug_unreachable_barrier; /* test knob: the first barrier can never complete */
+    int32_t data_term;             /* MVCT_DATA_WLS (0, default) or MVCT_DATA_POISSON (1) */
 } mvct_recon_opts;
+
+/* Data terms of mvct_recon (Sec. 2: Poisson photon statistics).
+ * WLS:     1/2 sum w_i ([A mu]_i - p_i)^2, the quadratic (log-domain) approximation.
+ * POISSON: sum w_i [A mu]_i + exp(-[A mu]_i), the negative Poisson log-likelihood
+ *          with counts y_i = I0 w_i divided by I0 (p is not used by its gradient).
+ * The adaptive lambda of Eq. 4-5 is driven by sum (A mu - p)^2 in both cases. */
+#define MVCT_DATA_WLS 0
+#define MVCT_DATA_POISSON 1
 
 /* Results of mvct_recon (host memory; arrays caller-owned, may be NULL). */
 typedef struct mvct_recon_stats {

@@ -50,6 +50,7 @@ class OracleParams(ctypes.Structure):
         ("tv_eps", ctypes.c_double),
         ("mu0", ctypes.c_double),
         ("init_from_input", ctypes.c_int32),
+        ("data_term", ctypes.c_int32),
     ]
 
 
@@ -133,8 +134,17 @@ def tv(img, eps: float, with_grad: bool = True):
 
 
 def objective(g, img, p, w, beta: float, eps: float) -> float:
+    """Weighted-least-squares objective Psi (see oracle_objective)."""
     return _load().oracle_objective(ctypes.byref(_geom(g)), _dp(_f64(img)), _dp(_f64(p)),
                                     _dp(_f64(w)), beta, eps)
+
+
+def poisson_objective(g, img, w, beta: float, eps: float) -> float:
+    """sum_i (w_i q_i + exp(-q_i)) + beta TV_eps: the negative Poisson log-likelihood
+    divided by I0 (counts y = I0 w, up to a constant), q = A img, plus the prior."""
+    q = forward(g, img)
+    wv = _f64(w).reshape(q.shape)
+    return float(np.sum(wv * q + np.exp(-q)) + beta * tv(img, eps, False)[0])
 
 
 def setup(g, w, beta: float, eps: float):
@@ -149,7 +159,7 @@ def setup(g, w, beta: float, eps: float):
 
 
 DEFAULTS = dict(lambda0=0.01, dlambda_up=1e-4, dlambda_down=2e-4, lambda_min=1e-4, kappa=100.0,
-                tv_eps=1e-6, mu0=0.05)
+                tv_eps=1e-6, mu0=0.05, data_term=0)
 
 
 def recon(g, n_subsets: int, p, w, beta: float, n_iter: int, init=None, lambda_schedule=None,
@@ -158,7 +168,7 @@ def recon(g, n_subsets: int, p, w, beta: float, n_iter: int, init=None, lambda_s
     prm = dict(DEFAULTS)
     prm.update(params)
     op = OracleParams(prm["lambda0"], prm["dlambda_up"], prm["dlambda_down"], prm["lambda_min"],
-                      prm["kappa"], prm["tv_eps"], prm["mu0"], 1 if init is not None else 0)
+                      prm["kappa"], prm["tv_eps"], prm["mu0"], 1 if init is not None else 0, prm["data_term"])
     img = np.zeros((g.n, g.n)) if init is None else _f64(init).reshape(g.n, g.n).copy()
     phi = np.zeros(max(n_iter, 1))
     lam = np.zeros(max(n_iter, 1))

@@ -50,6 +50,7 @@ typedef struct {
     double tv_eps;          /* smoothing inside the TV square root */
     double mu0;             /* homogeneous initial value, 1/cm (Sec. 3.3.2) */
     int32_t init_from_input;/* 1: start from the caller's image instead of mu0 */
+    int32_t data_term;      /* 0: weighted least squares on log projections; 1: Poisson log-likelihood */
 } oracle_recon_params;
 
 static const double PI = 3.14159265358979323846;
@@ -299,7 +300,11 @@ int oracle_setup(const oracle_geometry *g, const double *w, double beta, double 
  *
  * Sub-iteration n = 0 .. n_iter-1 uses subset s = n mod S:
  *   q   = A_s mu                         (reprojection of the subset's views)
- *   r   = q - p_s,  e = w_s .* r,  Phi_n = sum r^2 (the square difference)
+ *   r   = q - p_s,  Phi_n = sum r^2 (the square difference)
+ *   e   = w_s .* r                    (weighted least squares, data_term 0), or
+ *   e   = w_s - exp(-q)               (data_term 1: gradient of the negative Poisson
+ *                                      log-likelihood sum(y q + I0 exp(-q)) divided by
+ *                                      I0, with counts y = I0 w)
  *   lambda_n = lambda0 at n = 0; otherwise lambda_{n-1} + up if Phi_n < Phi_{n-1},
  *              - down if Phi_n > Phi_{n-1}, unchanged on a tie; floored at lambda_min.
  *              (lambda_schedule, if given, replaces the rule.)
@@ -345,7 +350,8 @@ int oracle_recon(const oracle_geometry *g, int n_subsets, const double *p, const
                 size_t i = (size_t)k * C + c, iv = (size_t)v * C + c;
                 double r = q[i] - p[iv];
                 phi += r * r;
-                q[i] = w[iv] * r;                   /* e, reusing q's storage */
+                q[i] = prm->data_term == 1 ? w[iv] - exp(-q[i])   /* e, reusing q's storage */
+                                           : w[iv] * r;
             }
         }
         phis[it] = phi;

@@ -52,6 +52,7 @@ struct LoopArgs {
     float eps;
     unsigned long long timeout_ns, spin_cap;
     int debug_unreachable;
+    int poisson;              // 1: Poisson data term, e = w - exp(-q)
 };
 
 } // namespace mvct

@@ -133,7 +133,8 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 const float q_ray = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
                 if (lane == 0) {
                     const float res = q_ray - pv;
-                    e4[ray] = make_float4(r.x, r.y, r.z * wv * res, r.w);
+                    const float ev = a.poisson ? wv - expf(-q_ray) : wv * res;
+                    e4[ray] = make_float4(r.x, r.y, r.z * ev, r.w);
                     acc_phi += (double)res * (double)res;
                 }
             }
@@ -463,7 +464,8 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     if (opts_in) o = *opts_in;
     else mvct_recon_opts_init(&o);
     if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
-        !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0))
+        !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
+        (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
         return mvct_fail(MVCT_EINVAL, "mvct_recon: invalid options");
     if (o.state && (o.state->n_done < 0 || (o.state->n_done > 0 && !o.init_from_input)))
         return mvct_fail(MVCT_EINVAL, "mvct_recon: resuming (state->n_done > 0) needs init_from_input = 1");
@@ -561,6 +563,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         a.timeout_ns = (unsigned long long)(o.barrier_timeout_ms * 1e6);
         a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
+        a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
         void *args[] = {&a};
         cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon<false>, dim3(P->recon_grid),
                                                      dim3(kThreads), args, 0, st);
@@ -784,7 +787,8 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
     if (o.lambda_schedule || o.state || o.d_best_out)
         return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: lambda_schedule, state and d_best_out are one-slice options");
     if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
-        !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0))
+        !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
+        (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
         return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: invalid options");
     for (int i = 0; i < b->count; ++i) {
         if (!d_sinos[i] || !d_weights[i] || !d_imgs[i])
@@ -882,6 +886,7 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
         a.timeout_ns = (unsigned long long)(o.barrier_timeout_ms * 1e6);
         a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
+        a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
         void *args[] = {&a};
         cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads),
                                                      args, 0, st);

@@ -72,6 +72,7 @@ class ReconOpts(ctypes.Structure):
         ("state", ctypes.POINTER(ReconState)),
         ("barrier_timeout_ms", ctypes.c_double),
         ("debug_unreachable_barrier", ctypes.c_int32),
+        ("data_term", ctypes.c_int32),
     ]
 
 

@@ -302,3 +302,42 @@ def test_noise_free_generator_gives_analytic_projection():
     li = ph.analytic_sinogram(c.geom, c.ellipses)
     assert np.allclose(c.p, li, rtol=1e-6, atol=1e-6)
     assert np.allclose(c.w, np.exp(-li), rtol=1e-6)
+
+
+def test_poisson_gradient_matches_finite_differences(A8):
+    """The Poisson data term's first step uses e = w - exp(-q): compare the step
+    with one built from a central finite-difference gradient of the negative
+    Poisson log-likelihood (divided by I0)."""
+    rng = np.random.default_rng(11)
+    w = rng.uniform(0.2, 1.0, (G8.n_views, G8.n_channels))
+    p = -np.log(w)
+    mu0 = rng.uniform(0.02, 0.1, (8, 8))
+    lam, S = 0.011, 1
+    r = oracle.recon(G8, S, p, w, 0.0, 1, init=mu0, lambda_schedule=[lam], data_term=1)
+    D, _ = oracle.setup(G8, w, 0.0, 1e-6)
+
+    def nll(x):
+        q = A8 @ x
+        return np.sum(w.ravel() * q + np.exp(-q))
+
+    h = 1e-6
+    grad = np.array([(nll(mu0.ravel() + h * e) - nll(mu0.ravel() - h * e)) / (2 * h) for e in np.eye(64)])
+    expect = np.maximum(0.0, mu0.ravel() - 100 * lam * D.ravel() * grad)
+    assert np.abs(r["image"].ravel() - expect).max() < 1e-8
+
+
+def test_poisson_term_reduces_to_wls_near_the_data(A8):
+    """With p = ln(1/w) exactly, w - exp(-q) = w (q - p) + O((q - p)^2): the two data
+    terms give the same first step to second order."""
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0.02, 0.1, (8, 8))
+    q = (A8 @ x.ravel()).reshape(G8.n_views, G8.n_channels)
+    w = np.exp(-q)
+    p = q.copy()
+    mu0 = x + 2e-5 * rng.normal(size=x.shape)
+    a = oracle.recon(G8, 1, p, w, 0.0, 1, init=mu0, lambda_schedule=[0.01], data_term=0)["image"]
+    b = oracle.recon(G8, 1, p, w, 0.0, 1, init=mu0, lambda_schedule=[0.01], data_term=1)["image"]
+    # the difference is second order in q - p (here |q - p| < 1e-3): relative 1e-3 of the step
+    dq = np.abs(A8 @ (mu0 - x).ravel()).max()
+    assert dq < 1e-3
+    assert np.abs(a - b).max() < dq * np.abs(a - mu0).max()
