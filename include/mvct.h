@@ -164,6 +164,15 @@ int mvct_recon(mvct_plan plan, const float *d_sino, const float *d_weights, doub
                int32_t n_iter, const mvct_recon_opts *opts, float *d_img_inout,
                mvct_recon_stats *stats, void *stream);
 
+/* Filtered backprojection (the paper's comparison image, Sec. 1 and 4.5, and the
+ * plain start image of the loop): equiangular fan-beam FBP with cosine
+ * pre-weighting D cos(gamma), the fan-beam ramp filter
+ * g(k a) = 1/2 (k a / sin(k a))^2 h(k a) (h the band-limited ramp, a the channel
+ * pitch) and 1/L^2-weighted backprojection over the full rotation, dbeta = 2 pi/V.
+ * d_sino: log projections [V][C] (all views); d_img: n*n output (1/cm).
+ * Uses the plan's scratch; asynchronous on stream. */
+int mvct_fbp(mvct_plan plan, const float *d_sino, float *d_img, void *stream);
+
 /* ---- Batches: many slices (uneven geometries) in one persistent launch ----
  * The plans (one per slice, all on one device, each in at most one batch) are
  * reconstructed together: the co-resident grid is split into block groups, each

@@ -117,7 +117,7 @@ void free_plan(mvct_plan_s *P)
     void *ptrs[] = {P->rays, P->views, P->a1t, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
                     P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
                     P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched,
-                    P->d_slice, P->d_group, P->d_block_group, P->d_count};
+                    P->d_slice, P->d_group, P->d_block_group, P->d_count, P->fbp_g, P->fbp_cos};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -203,6 +203,11 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     if (e != cudaSuccess) {
         free_plan(P);
         return mvct_fail(MVCT_ECUDA, "mvct_plan_create: %s", cudaGetErrorString(e));
+    }
+    rc = mvct_fbp_tables(P);
+    if (rc) {
+        free_plan(P);
+        return rc;
     }
     *out = P;
     return MVCT_OK;

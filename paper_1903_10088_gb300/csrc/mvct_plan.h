@@ -91,6 +91,9 @@ struct mvct_plan_s {
     int *d_block_group = nullptr;       // [recon_grid] zeros
     unsigned int *d_count = nullptr;    // group barrier counter
     bool in_batch = false;              // owned by a batch (its scratch is in use there)
+    float *fbp_g = nullptr;             // [2C-1] fan-beam ramp g(k a)
+    float *fbp_cos = nullptr;           // [C] D cos(gamma_c)
+    float fbp_a = 0.f;                  // channel pitch (rad)
     double *hist = nullptr;     // [2*hist_cap] phi and lambda per sub-iteration
     double *sched = nullptr;    // [hist_cap] lambda schedule
     int hist_cap = 0;
@@ -135,6 +138,9 @@ int recon_occupancy(mvct_plan_s *P);
 int slice_groups(const mvct_plan_s *P, int nblocks); // view groups per tile for a group of nblocks
 
 } // namespace mvct
+
+// FBP tables of a plan (mvct_fbp.cu).
+int mvct_fbp_tables(mvct_plan_s *P);
 
 // Error reporting shared by the translation units (mvct_api.cu).
 int mvct_fail(int code, const char *fmt, ...);

@@ -94,7 +94,7 @@ class ReconStats(ctypes.Structure):
 EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
            "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error",
            "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
-           "mvct_batch_run", "mvct_batch_stats"]
+           "mvct_batch_run", "mvct_batch_stats", "mvct_fbp"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -114,6 +114,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     lib.mvct_recon.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(ReconOpts), vp,
                                ctypes.POINTER(ReconStats), vp]
     lib.mvct_tv_grad_noalloc.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp]
+    lib.mvct_fbp.argtypes = [vp, vp, vp, vp]
     lib.mvct_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     lib.mvct_batch_destroy.argtypes = [vp]
     lib.mvct_batch_destroy.restype = None
@@ -221,6 +222,14 @@ class Plan:
         _check(lib().mvct_back(self._h, _dev_f32(sino, self.rows(subset) * self.C, "sino"),
                                _dev_f32(out, self.n * self.n, "out"), subset,
                                ctypes.c_void_p(_stream(stream))))
+        return out
+
+    def fbp(self, sino: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """``mvct_fbp``: fan-beam filtered backprojection of all views."""
+        if out is None:
+            out = torch.empty((self.n, self.n), device=sino.device, dtype=torch.float32)
+        _check(lib().mvct_fbp(self._h, _dev_f32(sino, self.V * self.C, "sino"), _dev_f32(out, self.n * self.n, "out"),
+                              ctypes.c_void_p(_stream(stream))))
         return out
 
     def tv_grad(self, img: torch.Tensor, eps: float, with_value: bool = True, stream=None):

@@ -148,8 +148,9 @@ def test_degenerate_geometries(mvct, geom):
 
 
 def test_full_size_projector_sampled(mvct):
-    """512^2, 800 views, 738 channels: every 37th ray of the full forward and a
-    sample of backprojected pixels against the oracle, ray by ray."""
+    """512^2, 800 views, 738 channels: the rows of one subset of the full-sinogram
+    projection and of the subset projection, and the subset backprojection, against
+    the oracle (one subset keeps the oracle to seconds)."""
     g = ph.GEOM_512
     img = phantom_image(g, 18)
     y = np.random.default_rng(19).uniform(0, 1, (g.n_views, g.n_channels)).astype(np.float32)
@@ -161,9 +162,7 @@ def test_full_size_projector_sampled(mvct):
     ref7 = oracle.forward(g, img.astype(np.float64), 7, 20)
     assert rel(qs, ref7) < RTOL_PROJ
     assert rel(q[7::20], ref7) < RTOL_PROJ
-    # back: oracle over 40 views compared with the GPU back of the same subset data
-    ys = np.zeros_like(y)
-    ys[7::20] = y[7::20]
+    # back: oracle over the 40 views of subset 7 against the GPU back of the same rows
     with mvct.Plan(g, 20) as plan:
         bs = host(plan.back(cuda(y[7::20].copy()), 7))
     refb = oracle.back(g, y[7::20].astype(np.float64), 7, 20)
@@ -177,3 +176,27 @@ def test_invalid_subset_rejected(mvct):
         with pytest.raises(mvct.MvctError):
             plan.forward(torch.zeros((g.n, g.n), device="cuda"), 10,
                          out=torch.zeros((20, g.n_channels), device="cuda"))
+
+
+@pytest.mark.parametrize("name", ["small", "offset"])
+def test_fbp_parity(mvct, name):
+    from oracle import fbp as F
+
+    g = GEOMS[name]
+    ell = ph.phantom_random_ellipses(31)
+    sino = ph.analytic_sinogram(g, ell).astype(np.float32)
+    with mvct.Plan(g, 1) as plan:
+        img = host(plan.fbp(cuda(sino)))
+    ref = F.fbp(g, sino.astype(np.float64))
+    assert rel(img, ref) < 1e-4
+
+
+def test_fbp_full_size_sampled(mvct):
+    """512^2, 800 x 738: the GPU FBP of a noisy full-size case against the oracle."""
+    from oracle import fbp as F
+
+    c = ph.make_case("full", 32)
+    with mvct.Plan(c.geom, 20) as plan:
+        img = host(plan.fbp(cuda(c.p)))
+    ref = F.fbp(c.geom, c.p.astype(np.float64))
+    assert rel(img, ref) < 1e-4
