@@ -211,6 +211,46 @@ int mvct_batch_run(mvct_batch batch, int32_t n_iter, void *stream);
  * failed. */
 int mvct_batch_stats(mvct_batch batch, int32_t slice, mvct_recon_stats *stats);
 
+/* ---- Learned warm start (a start image for mvct_recon from the FBP image) ----
+ * An 8-layer 3x3 convolutional network: 1 -> 32 channels, six 32 -> 32 layers,
+ * 32 -> 1, ReLU after layers 1-7, zero padding, residual output:
+ *   out = x + f(s x) / s   (s = the input scale given at creation),
+ * BF16 weights and activations with FP32 accumulation; the 32 -> 32 layers run
+ * on BF16 tensor cores in the forward and both backward convolutions. The
+ * network is trained on (FBP image, converged OS-TV image) pairs that the
+ * reconstruction itself produces; the paper (Sec. 3.3.2, 4.2) motivates it by
+ * the effect of the start image on convergence, and has no network of its own.
+ * Parameter vector (FP32, mvct_cnn_param_count() entries, host order):
+ *   W1[9][32] b1[32] | 6 x (W[9][32 in][32 out] b[32]) | W8[9][32] b8[1],
+ *   tap = 3*ky + kx, out[y][x] = sum x[y+ky-1][x+kx-1] W[tap] (cross-correlation). */
+typedef struct mvct_cnn_s *mvct_cnn;
+
+int32_t mvct_cnn_param_count(void);
+
+/* Network for batches of up to batch_max images of h x w on the current device;
+ * params: host array of initial parameters. Synchronous. */
+int mvct_cnn_create(int32_t batch_max, int32_t h, int32_t w, double scale, const float *params,
+                    mvct_cnn *out);
+void mvct_cnn_destroy(mvct_cnn cnn);
+
+/* Copy the FP32 master parameters to the host array params. Synchronous. */
+int mvct_cnn_get_params(mvct_cnn cnn, float *params);
+
+/* Inference: d_out[n][h][w] = network(d_in[n][h][w]) (FP32, device). */
+int mvct_cnn_forward(mvct_cnn cnn, const float *d_in, int32_t n, float *d_out, void *stream);
+
+/* Mean squared error of the network on (d_in, d_target) in the scaled domain,
+ * mean over all n*h*w pixels, written to *loss (host; the call synchronises
+ * the stream), and its gradient with respect to the parameters into d_grad
+ * (device, param_count floats) if not NULL. Deterministic. */
+int mvct_cnn_grad(mvct_cnn cnn, const float *d_in, const float *d_target, int32_t n, float *d_grad,
+                  double *loss, void *stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected) on the batch;
+ * *loss receives the batch loss before the step. Synchronises the stream. */
+int mvct_cnn_train_step(mvct_cnn cnn, const float *d_in, const float *d_target, int32_t n, double lr,
+                        double *loss, void *stream);
+
 /* Allocation-free variant of mvct_tv_grad for callers that may not allocate
  * device memory (applications that hand out all GPU memory through their own
  * allocator, or latency-critical paths where cudaMalloc/cudaFree, which can

@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmvct.so")
-SOURCES = ["mvct_api.cu", "mvct_kernels.cu", "mvct_recon.cu", "mvct_noalloc.cu", "mvct_fbp.cu"]
+SOURCES = ["mvct_api.cu", "mvct_kernels.cu", "mvct_recon.cu", "mvct_noalloc.cu", "mvct_fbp.cu", "mvct_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

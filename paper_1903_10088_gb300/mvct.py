@@ -94,7 +94,8 @@ class ReconStats(ctypes.Structure):
 EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
            "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error",
            "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
-           "mvct_batch_run", "mvct_batch_stats", "mvct_fbp"]
+           "mvct_batch_run", "mvct_batch_stats", "mvct_fbp", "mvct_cnn_param_count", "mvct_cnn_create",
+           "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -115,6 +116,17 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
                                ctypes.POINTER(ReconStats), vp]
     lib.mvct_tv_grad_noalloc.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp]
     lib.mvct_fbp.argtypes = [vp, vp, vp, vp]
+    fp = ctypes.POINTER(ctypes.c_float)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.mvct_cnn_param_count.argtypes = []
+    lib.mvct_cnn_param_count.restype = i32
+    lib.mvct_cnn_create.argtypes = [i32, i32, i32, ctypes.c_double, fp, ctypes.POINTER(vp)]
+    lib.mvct_cnn_destroy.argtypes = [vp]
+    lib.mvct_cnn_destroy.restype = None
+    lib.mvct_cnn_get_params.argtypes = [vp, fp]
+    lib.mvct_cnn_forward.argtypes = [vp, vp, i32, vp, vp]
+    lib.mvct_cnn_grad.argtypes = [vp, vp, vp, i32, vp, dp, vp]
+    lib.mvct_cnn_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_double, dp, vp]
     lib.mvct_batch_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     lib.mvct_batch_destroy.argtypes = [vp]
     lib.mvct_batch_destroy.restype = None
