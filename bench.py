@@ -33,10 +33,10 @@ if ROOT not in sys.path:
 
 from paper_1903_10088_gb300 import phantom as ph  # noqa: E402
 
-WORKLOAD = dict(workload="plain OS-TV, one 512^2 slice per step", n=512, fov_cm=40.0, n_views=800,
+WORKLOAD = dict(workload="plain OS-TV, one 512^2 slice per step (FBP start)", n=512, fov_cm=40.0, n_views=800,
                 n_channels=738, sad_cm=85.0, subsets=20, sub_iterations=500, beta=1e-3, tv_eps=1e-6,
                 I0=5e3, phantom="water disk + 7 low-contrast inserts + 4 rods (seeded)")
-METRIC = "512^2 slices/s at 500 OS-TV iters (plain); GRay/s; %HBM"
+METRIC = "512^2 slices/s at 500 OS-TV iters (plain vs warm-start+batched); GRay/s; %HBM"
 BATCH_WORKLOAD = dict(workload="batched uneven helical stack, 96 slices per step in one persistent launch",
                       slices="48 x 512^2 (800 views x 738 ch) + 32 x 384^2 (600 x 552) + 16 x 256^2 (400 x 368)",
                       fov_cm=40.0, sad_cm=85.0, subsets=20, sub_iterations=500, beta=1e-3, tv_eps=1e-6,
@@ -115,10 +115,10 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index: int, tag: str = ""):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}{tag}.csv")
 
     def __enter__(self):
         try:
@@ -200,11 +200,19 @@ def barrier():
 # CPU oracle timing (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
 def time_oracle(case, sub_iters: int):
-    """Oracle set-up + `sub_iters` sub-iterations; returns (seconds per slice
-    at the full sub-iteration count, sample description)."""
+    """Oracle FBP start + set-up + `sub_iters` sub-iterations; returns (seconds
+    per slice at the full sub-iteration count, sample description). The FBP is
+    timed on every tenth view and scaled (its cost is linear in the views)."""
+    import dataclasses
+
     import oracle
+    from oracle import fbp as ofbp
 
     oracle.build()
+    g10 = dataclasses.replace(case.geom, n_views=case.geom.n_views // 10)
+    t0 = time.perf_counter()
+    ofbp.fbp(g10, case.p[::10])
+    t_fbp = (time.perf_counter() - t0) * case.geom.n_views / g10.n_views
     t0 = time.perf_counter()
     oracle.setup(case.geom, case.w, case.beta, case.tv_eps)
     t_setup = time.perf_counter() - t0
@@ -212,9 +220,10 @@ def time_oracle(case, sub_iters: int):
     oracle.recon(case.geom, case.n_subsets, case.p, case.w, case.beta, sub_iters)  # set-up + loop
     t_run = time.perf_counter() - t0
     t_iter = max(t_run - t_setup, 1e-9) / sub_iters
-    t_slice = t_setup + case.n_iter * t_iter
-    sample = (f"FP64 oracle, 1 thread: set-up ({t_setup:.2f} s) + {sub_iters} sub-iterations "
-              f"({t_iter * 1e3:.1f} ms each) of the full-size workload, scaled to "
+    t_slice = t_fbp + t_setup + case.n_iter * t_iter
+    sample = (f"FP64 oracle, 1 thread: FBP start ({t_fbp:.2f} s, timed on {g10.n_views} of "
+              f"{case.geom.n_views} views and scaled), set-up ({t_setup:.2f} s) + {sub_iters} "
+              f"sub-iterations ({t_iter * 1e3:.1f} ms each) of the full-size workload, scaled to "
               f"{case.n_iter} sub-iterations per slice")
     return t_slice, sample
 
@@ -273,7 +282,9 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
 
     def step():
-        return plan.recon(p, w, case.beta, case.n_iter, img=img)
+        # the plain form: FBP start image, then the OS-TV loop
+        plan.fbp(p, out=img)
+        return plan.recon(p, w, case.beta, case.n_iter, img=img, init_from_input=True)
 
     for _ in range(args.warmup):
         step()
@@ -314,7 +325,7 @@ def run_ours(args):
         e0.record(stream)
         p.copy_(hp, non_blocking=True)
         w.copy_(hw, non_blocking=True)
-        plan.recon(p, w, case.beta, case.n_iter, img=img)
+        step()
         hout.copy_(img, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -343,7 +354,11 @@ def run_ours(args):
         t_slice, sample = time_oracle(case, args.ref_sub_iters)
         cpu = {"value": 1.0 / t_slice, "unit": "slices/s", "cores": 1, "kind": "oracle", "sample": sample}
 
-    launches_per_step = 3  # k_forward (set-up), k_setup_back, k_recon
+    warm = None
+    if not args.no_warm:
+        warm = run_warm(args, dev, ws, value)
+
+    launches_per_step = 6  # k_fbp_filter, k_fbp_back, k_forward + k_back_splat + k_setup_merge (set-up), k_recon
     line = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -362,6 +377,7 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "grid_blocks": res.grid_blocks,
+        "warm_start_batched": warm,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -369,6 +385,140 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return 0
+
+
+WARM_WORKLOAD = dict(workload="learned warm start + batched OS-TV: a stack of 48 held-out 512^2 slices per step",
+                     slices=48, n=512, n_views=800, n_channels=738, subsets=20, sub_iterations=80,
+                     lambda0=0.02, beta=1e-3, tv_eps=1e-6, I0=5e3,
+                     chain="FBP -> CNN (8 conv3x3, 32 ch, BF16 tensor cores) -> 80 OS-TV sub-iterations, "
+                           "all slices in one persistent launch, the whole chain one CUDA-graph replay",
+                     quality="objective Psi of every slice against the plain form (FBP start, 500 sub-iterations)")
+
+
+def run_warm(args, dev, ws, plain_slices_per_s):
+    """The warm-started, batched form: per step, FBP of every slice of the stack,
+    the network's start images, and K OS-TV sub-iterations of all slices in one
+    persistent launch, replayed as one CUDA graph. Quality: Psi of each slice
+    after the timed steps against the plain form's Psi (FBP start, 500
+    sub-iterations, computed after the timing)."""
+    import torch
+
+    from paper_1903_10088_gb300 import mvct
+    from paper_1903_10088_gb300 import warmstart as wst
+
+    B, K, lam0 = WARM_WORKLOAD["slices"], WARM_WORKLOAD["sub_iterations"], WARM_WORKLOAD["lambda0"]
+    _, rank, local = dist_env()
+    seeds = range(wst.HELDOUT_SEED0 + rank * B, wst.HELDOUT_SEED0 + (rank + 1) * B)
+    cases = wst.make_cases(seeds, workers=min(16, os.cpu_count() or 1))
+    g = cases[0].geom
+    plans = [mvct.Plan(g, cases[0].n_subsets) for _ in range(B)]
+    batch = mvct.Batch(plans)
+    P = torch.stack([torch.from_numpy(c.p) for c in cases]).to(dev)
+    W = torch.stack([torch.from_numpy(c.w) for c in cases]).to(dev)
+    X = torch.empty((B, g.n, g.n), device=dev)
+    IMG = torch.empty((B, g.n, g.n), device=dev)
+    betas = [c.beta for c in cases]
+    batch.bind(list(P), list(W), betas, list(IMG), K, init_from_input=True, lambda0=lam0)
+    cnn = wst.CNN(16, g.n, g.n, wst.load_weights())
+    s = torch.cuda.Stream()
+
+    def chain(st):
+        for k in range(B):
+            plans[k].fbp(P[k], out=X[k], stream=st)
+        wst.infer(cnn, X, out=IMG, stream=st)
+        batch.run(K, stream=st)
+
+    s.wait_stream(torch.cuda.current_stream())
+    chain(s)                                         # once outside capture
+    torch.cuda.synchronize()
+    batch.stats(0)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            chain(s)
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    batch.stats(0)                                   # raises if a run failed
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    cur = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local, "_warm") as clk:
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[k][0].record(cur)
+            graph.replay()
+            ev[k][1].record(cur)
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_max = max_over_ranks(float(np.sum(step_ms)), dev)
+    value = B * ws * args.steps / (t_max / 1e3)
+
+    # stage times of one untimed chain (events between the stages)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record(cur)
+    for k in range(B):
+        plans[k].fbp(P[k], out=X[k])
+    e[1].record(cur)
+    wst.infer(cnn, X, out=IMG)
+    e[2].record(cur)
+    batch.run(K)
+    e[3].record(cur)
+    torch.cuda.synchronize()
+    stage_ms = {"fbp": e[0].elapsed_time(e[1]) / B, "cnn": e[1].elapsed_time(e[2]) / B,
+                "setup_and_loop": e[2].elapsed_time(e[3]) / B}
+
+    # end to end: host sinograms and weights in, host images out
+    hP, hW = P.cpu().pin_memory(), W.cpu().pin_memory()
+    hI = torch.empty_like(IMG, device="cpu").pin_memory()
+    e2e_ms = []
+    for k in range(max(1, args.steps)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        P.copy_(hP, non_blocking=True)
+        W.copy_(hW, non_blocking=True)
+        graph.replay()
+        hI.copy_(IMG, non_blocking=True)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = max_over_ranks(float(np.sum(e2e_ms)), dev)
+
+    # quality: Psi of the warm-started results against the plain form
+    psi = lambda k, im: float(plans[0].objective(im, P[k], W[k], cases[k].beta, cases[k].tv_eps).item())
+    psi_warm = np.array([psi(k, IMG[k]) for k in range(B)])
+    graph = None
+    for k in range(B):
+        plans[k].fbp(P[k], out=IMG[k])
+    batch.bind(list(P), list(W), betas, list(IMG), 500, init_from_input=True)
+    batch.run(500)
+    batch.stats(0)
+    psi_plain = np.array([psi(k, IMG[k]) for k in range(B)])
+    gap = (psi_warm - psi_plain) / psi_plain
+    cnn.close()
+    batch.close()
+    for pl in plans:
+        pl.close()
+    return {
+        "value": value, "unit": "slices/s", "ms_per_step": t_max / args.steps,
+        "speedup_vs_plain": value / plain_slices_per_s if plain_slices_per_s else None,
+        "config": dict(WARM_WORKLOAD, seeds=[seeds[0], seeds[-1]],
+                       weights="paper_1903_10088_gb300/weights/warmstart_512.npy",
+                       l2="flushed between timed steps (512 MiB write)"),
+        "stage_ms_per_slice": stage_ms,
+        "psi_gap_vs_plain": {"median": float(np.median(gap)), "max": float(gap.max()), "min": float(gap.min()),
+                             "within_1e-3": float(np.mean(gap <= 1e-3))},
+        "e2e": {"value": B * ws * len(e2e_ms) / (e2e_t / 1e3), "unit": "slices/s",
+                "h2d_bytes_per_step": int(hP.numel() * 4 + hW.numel() * 4),
+                "d2h_bytes_per_step": int(hI.numel() * 4)},
+        "gpu_launches_per_step": 2 * B + 10 * ((B + 15) // 16) + 2 + 3 * B,
+        "clocks": clk.summary(),
+    }
 
 
 def _make_batch_case(args):
@@ -433,7 +583,7 @@ def run_batched(args):
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with ClockSampler(local, "_batched") as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(cur)
@@ -466,7 +616,7 @@ def run_batched(args):
                      "kernel": "k_recon<batch> + set-up (whole graph)",
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
         "clocks": clk.summary(),
-        "gpu_launches": (1 + 3 * len(cases)) * args.steps,
+        "gpu_launches": (2 + 3 * len(cases)) * args.steps,
     }
     if rank == 0:
         print(json.dumps(line))
@@ -487,6 +637,7 @@ def main(argv=None):
     ap.add_argument("--ref-sub-iters", type=int, default=40,
                     help="oracle sub-iterations timed per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm", action="store_true", help="skip the warm-started batched form")
     ap.add_argument("--workload", choices=["plain", "batched"], default="plain")
     args = ap.parse_args(argv)
     if args.impl == "reference":

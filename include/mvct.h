@@ -207,8 +207,9 @@ int mvct_batch_run(mvct_batch batch, int32_t n_iter, void *stream);
 /* Synchronise the device, then fill *stats (may be NULL) for one slice (plan
  * order) of the last run: Phi and lambda per sub-iteration, best pass, and the
  * device times of the whole batch (setup_ms, loop_ms; -1 after a CUDA-graph
- * replay of mvct_batch_run). Returns MVCT_ETIMEOUT / MVCT_EDATA if the run
- * failed. */
+ * replay of mvct_batch_run). stats->phi and stats->lambda, when not NULL, must
+ * each hold the last run's n_iter doubles (caller-owned host memory). Returns
+ * MVCT_ETIMEOUT / MVCT_EDATA if the run failed. */
 int mvct_batch_stats(mvct_batch batch, int32_t slice, mvct_recon_stats *stats);
 
 /* ---- Learned warm start (a start image for mvct_recon from the FBP image) ----

@@ -150,16 +150,20 @@ __global__ void __launch_bounds__(256) k_conv32(const __nv_bfloat16 *__restrict_
     }
 }
 
-// ---- weight gradient of a 32 -> 32 layer on tensor cores -------------------
+// ---- weight and bias gradient of a 32 -> 32 layer on tensor cores ---------
 // part[block][tap][ci][co] = sum over the block's pixels p of
 //   a[p + off(tap)][ci] * d[p][co]   (a: layer input, d: pre-activation gradient)
-// One warp per tap (9 warps); blocks stride over the output tiles.
+// part[block][9*32*32 + co] = sum over the block's pixels of d[p][co]
+// (the row stride of part is MID_SIZE, the layer's slice of the parameter vector).
+// One warp per tap (9 warps) on the tensor cores; warps 0-7 also sum the bias
+// gradient, one tile row each. Blocks stride over the output tiles.
 __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ a,
                                               const __nv_bfloat16 *__restrict__ d, float *__restrict__ part,
                                               int N, int H, int W)
 {
     __shared__ __align__(16) __nv_bfloat16 s_a[(TH + 2) * (TW + 2) * SPAD];
     __shared__ __align__(16) __nv_bfloat16 s_d[TH * TW * SPAD];
+    __shared__ float s_b[TH][CH];
     const int tid = threadIdx.x, lane = tid & 31, tap = tid >> 5;
     const int ky = tap / 3, kx = tap - 3 * (tap / 3);
     const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ 
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+    float bsum = 0.f; // warps 0-7: channel `lane` of tile row `tap`
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int n = tile / (tiles_x * tiles_y), rem = tile - n * tiles_x * tiles_y;
         const int y0 = (rem / tiles_x) * TH, x0 = (rem % tiles_x) * TW;
@@ -192,6 +197,10 @@ __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ 
             *((uint4 *)(s_d + px * SPAD) + q) = v;
         }
         __syncthreads();
+        if (tap < TH) {
+#pragma unroll 4
+            for (int j = 0; j < TW; ++j) bsum += __bfloat162float(s_d[(tap * TW + j) * SPAD + lane]);
+        }
 #pragma unroll 1
         for (int r = 0; r < TH; ++r) { // k-step: the 16 pixels of output row r
             const int q = lane >> 3, rr = lane & 7;
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ 
     }
     // write this block's partial: rows ci = mt*16 + g (+8), cols co = nt*8 + 2t (+1)
     const int g = lane >> 2, t = lane & 3;
-    float *dst = part + ((size_t)blockIdx.x * 9 + tap) * CH * CH;
+    float *dst = part + (size_t)blockIdx.x * MID_SIZE + tap * CH * CH;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -227,16 +236,36 @@ __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ 
             dst[(ci + 8) * CH + co] = acc[mt][nt][2];
             dst[(ci + 8) * CH + co + 1] = acc[mt][nt][3];
         }
+    if (tap < TH) s_b[tap][lane] = bsum;
+    __syncthreads();
+    if (tid < CH) {
+        float sb = 0.f;
+#pragma unroll
+        for (int r = 0; r < TH; ++r) sb += s_b[r][tid];
+        part[(size_t)blockIdx.x * MID_SIZE + 9 * CH * CH + tid] = sb;
+    }
 }
 
-// out[k] = sum over b < nb of part[b][k] (fixed order), k < len.
-__global__ void k_reduce_parts(const float *__restrict__ part, int nb, int len, float *__restrict__ out)
+// out[k] = sum over b < nb of part[b * stride + k], k < len, in a fixed order:
+// warp w of a block sums b = w, w + 8, ... for 32 consecutive k (one per lane),
+// then the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_reduce_parts(const float *__restrict__ part, int nb, int len, int stride,
+                                                      float *__restrict__ out)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= len) return;
-    float s = 0.f;
-    for (int b = 0; b < nb; ++b) s += part[(size_t)b * len + k];
-    out[k] = s;
+    __shared__ float s[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + lane;
+    float acc = 0.f;
+    if (k < len)
+        for (int b = warp; b < nb; b += 8) acc += __ldg(part + (size_t)b * stride + k);
+    s[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && k < len) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += s[w][lane];
+        out[k] = t;
+    }
 }
 
 // ---- first layer: 1 -> 32 (CUDA cores) -------------------------------------
@@ -358,81 +387,87 @@ __global__ void __launch_bounds__(256) k_conv_out_bwd(const float *__restrict__ 
     }
 }
 
-// Per-block partials of the weight / bias gradients of the 1-channel layers:
-//   mode 0 (first layer): part[b][tap*32 + co] = sum_p x[p + off] d1[p][co], part[b][288 + co] = sum_p d1[p][co]
-//   mode 1 (last layer):  part[b][tap*32 + ci] = sum_p a7[p + off][ci] dout[p], part[b][288] = sum_p dout[p]
+// Per-block partials of the weight / bias gradients of the 1-channel layers
+// (row stride EDGE_LEN):
+//   MODE 0 (first layer): part[b][tap*32 + co] = sum_p xs[p + off] d1[p][co],
+//                          part[b][288 + co]   = sum_p d1[p][co]
+//   MODE 1 (last layer):  part[b][tap*32 + ci] = sum_p a7[p + off][ci] dout[p],
+//                          part[b][288]        = sum_p dout[p] (289 .. 319 zero)
+// narrow = xs / dout: FP32 padded [N][H+2][W+2]; wide = d1 / a7: BF16 padded
+// NHWC. 320 threads: warp w < 9 owns tap w (lane = channel), warp 9 the bias.
+// Blocks stride over 8 x 16 output tiles staged in shared memory, the shifted
+// operand with its one-pixel halo.
+constexpr int EDGE_LEN = 9 * CH + CH;
 template <int MODE>
-__global__ void __launch_bounds__(256) k_dw_edge(const float *__restrict__ xs, const __nv_bfloat16 *__restrict__ act,
-                                                 float *__restrict__ part, int N, int H, int W)
+__global__ void __launch_bounds__(320) k_dw_edge(const float *__restrict__ narrow,
+                                                 const __nv_bfloat16 *__restrict__ wide, float *__restrict__ part,
+                                                 int N, int H, int W)
 {
-    constexpr int LEN = 9 * CH + CH;
-    __shared__ float s_acc[8][LEN];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc[10]; // lane owns channel `lane`: 9 taps + bias
-#pragma unroll
-    for (int k = 0; k < 10; ++k) acc[k] = 0.f;
-    const long long total = (long long)N * H * W;
-    for (long long pidx = (long long)blockIdx.x * 8 + warp; pidx < total; pidx += (long long)gridDim.x * 8) {
-        const int n = (int)(pidx / ((long long)H * W));
-        const int rem = (int)(pidx - (long long)n * H * W), yy = rem / W, xx = rem - yy * W;
-        if (MODE == 0) {
-            const float dv = __bfloat162float(act[apix(n, yy, xx, H, W) * CH + lane]);
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap)
-                acc[tap] = fmaf(__ldg(xs + apix(n, yy + tap / 3 - 1, xx + tap % 3 - 1, H, W)), dv, acc[tap]);
-            acc[9] += dv;
+    constexpr int HP = (TH + 2) * (TW + 2);      // halo tile pixels
+    constexpr int WP = MODE == 1 ? HP : TH * TW; // pixels of the staged wide tile
+    constexpr int NP = MODE == 1 ? TH * TW : HP; // pixels of the staged narrow tile
+    __shared__ __align__(16) __nv_bfloat16 s_w[WP * CH];
+    __shared__ float s_n[NP];
+    __shared__ float s_r[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tiles_x = (W + TW - 1) / TW, tiles_y = (H + TH - 1) / TH;
+    const int n_tiles = N * tiles_x * tiles_y;
+    const int ky = warp / 3, kx = warp - 3 * (warp / 3);
+    float acc = 0.f;
+    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int n = tile / (tiles_x * tiles_y), rem = tile - n * tiles_x * tiles_y;
+        const int y0 = (rem / tiles_x) * TH, x0 = (rem % tiles_x) * TW;
+        __syncthreads();
+        for (int k = tid; k < WP * 4; k += 320) {
+            const int px = k >> 2, q = k & 3;
+            const int tw = MODE == 1 ? TW + 2 : TW, o = MODE == 1 ? 1 : 0;
+            const int ty = px / tw, tx = px - ty * tw;
+            const int gy = y0 + ty - o, gx = x0 + tx - o;
+            const bool ok = MODE == 1 ? (gy <= H && gx <= W) : (gy < H && gx < W);
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (ok) v = *((const uint4 *)(wide + apix(n, gy, gx, H, W) * CH) + q);
+            *((uint4 *)(s_w + px * CH) + q) = v;
+        }
+        for (int px = tid; px < NP; px += 320) {
+            const int tw = MODE == 0 ? TW + 2 : TW, o = MODE == 0 ? 1 : 0;
+            const int ty = px / tw, tx = px - ty * tw;
+            const int gy = y0 + ty - o, gx = x0 + tx - o;
+            const bool ok = MODE == 0 ? (gy <= H && gx <= W) : (gy < H && gx < W);
+            s_n[px] = ok ? __ldg(narrow + apix(n, gy, gx, H, W)) : 0.f;
+        }
+        __syncthreads();
+        if (warp < 9) {
+#pragma unroll 4
+            for (int p = 0; p < TH * TW; ++p) {
+                const int py = p / TW, pxx = p - py * TW;
+                const int hp = (py + ky) * (TW + 2) + pxx + kx; // the shifted pixel in the halo tile
+                if (MODE == 1)
+                    acc = fmaf(__bfloat162float(s_w[hp * CH + lane]), s_n[p], acc);
+                else
+                    acc = fmaf(s_n[hp], __bfloat162float(s_w[p * CH + lane]), acc);
+            }
+        } else if (MODE == 0) {
+#pragma unroll 4
+            for (int p = 0; p < TH * TW; ++p) acc += __bfloat162float(s_w[p * CH + lane]);
         } else {
-            const float dv = __ldg(xs + apix(n, yy, xx, H, W));
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap)
-                acc[tap] = fmaf(__bfloat162float(act[apix(n, yy + tap / 3 - 1, xx + tap % 3 - 1, H, W) * CH + lane]),
-                                dv, acc[tap]);
-            acc[9] += dv; // every lane adds the same value: lane 0's copy is used
+            for (int p = lane; p < TH * TW; p += 32) acc += s_n[p];
         }
     }
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) s_acc[warp][tap * CH + lane] = acc[tap];
-    s_acc[warp][9 * CH + lane] = acc[9];
-    __syncthreads();
-    for (int k = threadIdx.x; k < LEN; k += 256) {
-        float s = 0.f;
-        for (int w = 0; w < 8; ++w) s += s_acc[w][k];
-        part[(size_t)blockIdx.x * LEN + k] = s;
-    }
-}
-
-// Bias gradient partials of a 32 -> 32 layer: part[b][co] = sum_p d[p][co].
-__global__ void __launch_bounds__(256) k_db32(const __nv_bfloat16 *__restrict__ d, float *__restrict__ part, int N,
-                                              int H, int W)
-{
-    __shared__ float s_acc[8][CH];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float acc = 0.f;
-    const long long total = (long long)N * H * W;
-    for (long long pidx = (long long)blockIdx.x * 8 + warp; pidx < total; pidx += (long long)gridDim.x * 8) {
-        const int n = (int)(pidx / ((long long)H * W));
-        const int rem = (int)(pidx - (long long)n * H * W), yy = rem / W, xx = rem - yy * W;
-        acc += __bfloat162float(d[apix(n, yy, xx, H, W) * CH + lane]);
-    }
-    s_acc[warp][lane] = acc;
-    __syncthreads();
-    if (threadIdx.x < CH) {
-        float s = 0.f;
-        for (int w = 0; w < 8; ++w) s += s_acc[w][threadIdx.x];
-        part[(size_t)blockIdx.x * CH + threadIdx.x] = s;
-    }
-}
-
-// Scatter the reduced edge-layer gradients into the parameter-gradient vector.
-__global__ void k_edge_to_grad(const float *__restrict__ red, int mode, float *__restrict__ grad)
-{
-    const int k = threadIdx.x + blockIdx.x * blockDim.x;
-    if (mode == 0) {
-        if (k < 9 * CH) grad[OFF_W1 + k] = red[k];
-        else if (k < 10 * CH) grad[OFF_B1 + k - 9 * CH] = red[k];
+    float *dst = part + (size_t)blockIdx.x * EDGE_LEN;
+    if (warp < 9) {
+        dst[warp * CH + lane] = acc;
+    } else if (MODE == 0) {
+        dst[9 * CH + lane] = acc;
     } else {
-        if (k < 9 * CH) grad[OFF_W8 + k] = red[k];
-        else if (k == 9 * CH) grad[OFF_B8] = red[9 * CH]; // lane 0's bias sum
+        s_r[lane] = acc;
+        __syncwarp();
+        if (lane == 0) {
+            float t = 0.f;
+            for (int k = 0; k < 32; ++k) t += s_r[k];
+            dst[9 * CH] = t;
+        } else {
+            dst[9 * CH + lane] = 0.f;
+        }
     }
 }
 
@@ -583,30 +618,27 @@ int cnn_backward(mvct_cnn_s *c, int n, cudaStream_t st)
     const int H = c->H, W = c->W;
     const long long pix = (long long)n * H * W;
     const int PB = c->part_blocks;
-    constexpr int LEN_EDGE = 9 * CH + CH;
-    // last layer: weight gradient and input gradient (masked by a7)
-    k_dw_edge<1><<<PB, 256, 0, st>>>(c->dout, c->act[6], c->part, n, H, W);
-    k_reduce_parts<<<(LEN_EDGE + 255) / 256, 256, 0, st>>>(c->part, PB, LEN_EDGE, c->part + (size_t)PB * LEN_EDGE);
-    k_edge_to_grad<<<2, 256, 0, st>>>(c->part + (size_t)PB * LEN_EDGE, 1, c->g);
+    // last layer: weight and bias gradient (W8 and b8 are contiguous in the
+    // parameter vector), then the input gradient masked by a7
+    k_dw_edge<1><<<PB, 320, 0, st>>>(c->dout, c->act[6], c->part, n, H, W);
+    k_reduce_parts<<<(9 * CH + 1 + 31) / 32, 256, 0, st>>>(c->part, PB, 9 * CH + 1, EDGE_LEN, c->g + OFF_W8);
     k_conv_out_bwd<<<grid_for(c, pix, 256), 256, 0, st>>>(c->dout, c->wf + OFF_W8, c->act[6], c->dgrad[0], n, H, W);
     const dim3 tg((W + TW - 1) / TW, (H + TH - 1) / TH, n);
     int cur = 0;
     for (int l = MID - 1; l >= 0; --l) {
-        // layer l+2 (0-based mid index l): input act[l], pre-activation gradient dgrad[cur]
-        float *gw = c->g + OFF_MID + l * MID_SIZE;
+        // layer l+2 (0-based mid index l): input act[l], pre-activation gradient dgrad[cur];
+        // weights then bias, contiguous in the parameter vector
         k_dw32<<<PB, 288, 0, st>>>(c->act[l], c->dgrad[cur], c->part, n, H, W);
-        k_reduce_parts<<<(9 * CH * CH + 255) / 256, 256, 0, st>>>(c->part, PB, 9 * CH * CH, gw);
-        k_db32<<<PB, 256, 0, st>>>(c->dgrad[cur], c->part, n, H, W);
-        k_reduce_parts<<<1, CH, 0, st>>>(c->part, PB, CH, gw + 9 * CH * CH);
+        k_reduce_parts<<<(MID_SIZE + 31) / 32, 256, 0, st>>>(c->part, PB, MID_SIZE, MID_SIZE,
+                                                            c->g + OFF_MID + l * MID_SIZE);
         // input gradient, masked by the previous activation (act[l])
         k_conv32<1><<<tg, 256, 0, st>>>(c->dgrad[cur], c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l],
                                         c->dgrad[cur ^ 1], H, W);
         cur ^= 1;
     }
-    // first layer: weight and bias gradient from the scaled input
-    k_dw_edge<0><<<PB, 256, 0, st>>>(c->xs, c->dgrad[cur], c->part, n, H, W);
-    k_reduce_parts<<<(LEN_EDGE + 255) / 256, 256, 0, st>>>(c->part, PB, LEN_EDGE, c->part + (size_t)PB * LEN_EDGE);
-    k_edge_to_grad<<<2, 256, 0, st>>>(c->part + (size_t)PB * LEN_EDGE, 0, c->g);
+    // first layer: weight and bias gradient (W1 and b1 contiguous) from the scaled input
+    k_dw_edge<0><<<PB, 320, 0, st>>>(c->xs, c->dgrad[cur], c->part, n, H, W);
+    k_reduce_parts<<<(EDGE_LEN + 31) / 32, 256, 0, st>>>(c->part, PB, EDGE_LEN, EDGE_LEN, c->g + OFF_W1);
     CKC(cudaGetLastError());
     return MVCT_OK;
 }
@@ -652,7 +684,7 @@ extern "C" int mvct_cnn_create(int32_t nmax, int32_t h, int32_t w, double scale,
     alloc((void **)&c->dout, sizeof(float) * padpix);
     for (auto &a : c->act) alloc((void **)&a, sizeof(__nv_bfloat16) * padpix * CH);
     for (auto &d : c->dgrad) alloc((void **)&d, sizeof(__nv_bfloat16) * padpix * CH);
-    alloc((void **)&c->part, sizeof(float) * ((size_t)c->part_blocks + 1) * 9 * CH * CH);
+    alloc((void **)&c->part, sizeof(float) * (size_t)c->part_blocks * MID_SIZE);
     alloc((void **)&c->loss_part, sizeof(double) * c->num_sms * 8);
     ok = ok && cudaMallocHost((void **)&c->h_loss, sizeof(double) * c->num_sms * 8) == cudaSuccess;
     if (!ok) {

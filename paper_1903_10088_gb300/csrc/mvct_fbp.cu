@@ -32,8 +32,29 @@ __global__ void __launch_bounds__(kThreads) k_fbp_filter(Geo g, const float *__r
     }
 }
 
+// arctan(t) for |t| <= 0.42 from its Taylor (Gregory) series
+// t - t^3/3 + t^5/5 - ... through the t^17 term, in Horner form in z = t^2;
+// the first omitted term is below 0.42^19 / 19 < 4e-9 rad.
+__device__ __forceinline__ float atan_series(float t)
+{
+    const float z = t * t;
+    float s = 1.f / 17.f;
+    s = fmaf(s, z, -1.f / 15.f);
+    s = fmaf(s, z, 1.f / 13.f);
+    s = fmaf(s, z, -1.f / 11.f);
+    s = fmaf(s, z, 1.f / 9.f);
+    s = fmaf(s, z, -1.f / 7.f);
+    s = fmaf(s, z, 1.f / 5.f);
+    s = fmaf(s, z, -1.f / 3.f);
+    s = fmaf(s, z, 1.f);
+    return t * s;
+}
+
 // One thread per pixel: f = dbeta * sum_v Q(beta_v, gamma'(x, y)) / L^2, Q linearly
-// interpolated in gamma (0 outside the detector), views in order.
+// interpolated in gamma (0 outside the detector), views in order. The ray angle
+// gamma' = atan(crs / dot) comes from the series above when |crs / dot| <= 0.42
+// (every pixel of a clinical fan, whose half-angle is about 0.24 rad) and from
+// atan2f otherwise.
 __global__ void __launch_bounds__(kThreads) k_fbp_back(Geo g, const float4 *__restrict__ views,
                                                       const float *__restrict__ q, float dbeta,
                                                       float *__restrict__ img)
@@ -48,14 +69,16 @@ __global__ void __launch_bounds__(kThreads) k_fbp_back(Geo g, const float4 *__re
             const float px = x - vw.x, py = y - vw.y;
             const float dot = fmaf(px, vw.z, py * vw.w);
             const float crs = fmaf(vw.z, py, -vw.w * px);
-            const float u = fmaf(atan2f(crs, dot), g.inv_dgamma, g.c_mid);
+            const float t = __fdividef(crs, dot);
+            const float ang = (dot > 0.f && fabsf(t) <= 0.42f) ? atan_series(t) : atan2f(crs, dot);
+            const float u = fmaf(ang, g.inv_dgamma, g.c_mid);
             const float fl = floorf(u);
             const int k0 = (int)fl;
             const float f = u - fl;
             const float *qv = q + (size_t)v * g.C;
             const float a0 = ((unsigned)k0 < (unsigned)g.C) ? __ldg(qv + k0) : 0.f;
             const float a1 = ((unsigned)(k0 + 1) < (unsigned)g.C) ? __ldg(qv + k0 + 1) : 0.f;
-            acc = fmaf(fmaf(f, a1 - a0, a0), 1.f / fmaf(dot, dot, crs * crs), acc);
+            acc = fmaf(fmaf(f, a1 - a0, a0), __fdividef(1.f, fmaf(dot, dot, crs * crs)), acc);
         }
         img[r] = dbeta * acc;
     }

@@ -326,6 +326,7 @@ class Batch:
         self._h = h
         self._keep = None
         self.max_iter = 0
+        self.last_n_iter = 0
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -365,8 +366,13 @@ class Batch:
 
     def run(self, n_iter: int, stream=None):
         _check(lib().mvct_batch_run(self._h, n_iter, ctypes.c_void_p(_stream(stream))))
+        self.last_n_iter = n_iter
 
-    def stats(self, i: int, n_iter: int) -> ReconResult:
+    def stats(self, i: int, n_iter: Optional[int] = None) -> ReconResult:
+        """Statistics of slice i of the last run (its n_iter sub-iterations)."""
+        if n_iter is not None and n_iter != self.last_n_iter:
+            raise ValueError(f"the last run had {self.last_n_iter} sub-iterations, not {n_iter}")
+        n_iter = self.last_n_iter
         phi = np.zeros(max(n_iter, 1))
         lam = np.zeros(max(n_iter, 1))
         st = ReconStats()

@@ -100,3 +100,315 @@ class CNN:
                                                          lr, ctypes.byref(loss),
                                                          ctypes.c_void_p(self._m._stream(stream))))
         return loss.value
+
+
+# ---------------------------------------------------------------------------
+# Training pairs generated by the method, training, inference
+# ---------------------------------------------------------------------------
+TRAIN_SEED0 = 30_000     # training phantoms: seeds TRAIN_SEED0 ..
+HELDOUT_SEED0 = 50_000   # held-out phantoms: seeds HELDOUT_SEED0 ..
+N_ITER_TARGET = 500
+
+
+def case_for(seed, kind: str = "full"):
+    """The seeded case of `kind` ("full": 512^2, 800 views x 738 channels,
+    inserts and rods, I0 = 5e3; "small": 128^2, 200 x 184, random ellipses)."""
+    from . import phantom as ph
+
+    return ph.make_case(kind, seed)
+
+
+def make_cases(seeds, kind: str = "full", workers: int = 8):
+    """Seeded cases generated on the host in spawned worker processes."""
+    import concurrent.futures as cf
+    import functools
+    import multiprocessing as mp
+
+    seeds = list(seeds)
+    if workers <= 1 or len(seeds) < 4:
+        return [case_for(s, kind) for s in seeds]
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(functools.partial(case_for, kind=kind), seeds, chunksize=4))
+
+
+class StackReconstructor:
+    """FBP and batched OS-TV reconstructions of stacks of same-geometry slices:
+    `width` plans in one :class:`mvct.Batch`, re-bound for every chunk."""
+
+    def __init__(self, geom, n_subsets: int, width: int, device):
+        import torch
+
+        from . import mvct
+
+        self.geom, self.width, self.device = geom, width, device
+        self.plans = [mvct.Plan(geom, n_subsets) for _ in range(width)]
+        self.batch = mvct.Batch(self.plans)
+        R = (geom.n_views, geom.n_channels)
+        self.p = [torch.empty(R, device=device) for _ in range(width)]
+        self.w = [torch.empty(R, device=device) for _ in range(width)]
+        self.img = [torch.empty((geom.n, geom.n), device=device) for _ in range(width)]
+
+    def close(self):
+        self.batch.close()
+        for p in self.plans:
+            p.close()
+
+    def load(self, cases):
+        """Copy the sinograms and weights of up to `width` cases to the device."""
+        for k, c in enumerate(cases):
+            self.p[k].copy_(_torch().from_numpy(c.p))
+            self.w[k].copy_(_torch().from_numpy(c.w))
+
+    def fbp(self, k: int, out):
+        return self.plans[0].fbp(self.p[k], out=out)
+
+    def run(self, count: int, betas, starts, n_iter: int, stream=None, **opts):
+        """OS-TV of the first `count` loaded slices from `starts` (list of
+        images; None = the loop's homogeneous start). Results in self.img."""
+        torch = _torch()
+        for k in range(self.width):
+            if k < count and starts is not None:
+                self.img[k].copy_(starts[k])
+            elif k >= count:
+                # unused lanes reconstruct a copy of slice 0 (results ignored)
+                self.p[k].copy_(self.p[0])
+                self.w[k].copy_(self.w[0])
+                if starts is not None:
+                    self.img[k].copy_(starts[0])
+        b = list(betas) + [betas[0]] * (self.width - count)
+        self.batch.bind(self.p, self.w, b, self.img, n_iter, init_from_input=starts is not None, **opts)
+        self.batch.run(n_iter, stream=stream)
+        self.batch.stats(0)             # waits; raises on a data or barrier error
+        torch.cuda.synchronize()
+        return self.img[:count]
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def make_pairs(seeds, device, width: int = 96, n_iter: int = N_ITER_TARGET, workers: int = 8, log=None,
+               kind: str = "full"):
+    """(FBP images, n_iter-iteration OS-TV images from the FBP start) for the
+    seeded cases, both [N][n][n] FP32 on `device`: the pairs the network learns.
+    The host generates the next chunk of cases while the GPU reconstructs one."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import time
+
+    torch = _torch()
+    seeds = list(seeds)
+    ex = cf.ProcessPoolExecutor(max(1, workers), mp_context=mp.get_context("spawn"))
+    chunks = [seeds[c0:c0 + width] for c0 in range(0, len(seeds), width)]
+    submit = lambda ch: [ex.submit(case_for, s, kind) for s in ch]
+    t_wait = t_gpu = 0.0
+    rec = X = Y = None
+    try:
+        pending = submit(chunks[0])
+        done = 0
+        for ci, ch in enumerate(chunks):
+            t0 = time.perf_counter()
+            cases = [f.result() for f in pending]
+            t_wait += time.perf_counter() - t0
+            pending = submit(chunks[ci + 1]) if ci + 1 < len(chunks) else []
+            if rec is None:
+                g = cases[0].geom
+                X = torch.empty((len(seeds), g.n, g.n), device=device)
+                Y = torch.empty_like(X)
+                rec = StackReconstructor(g, cases[0].n_subsets, min(width, len(seeds)), device)
+            t0 = time.perf_counter()
+            rec.load(cases)
+            for k in range(len(cases)):
+                rec.fbp(k, X[done + k])
+            out = rec.run(len(cases), [c.beta for c in cases], [X[done + k] for k in range(len(cases))], n_iter)
+            for k in range(len(cases)):
+                Y[done + k].copy_(out[k])
+            torch.cuda.synchronize()
+            t_gpu += time.perf_counter() - t0
+            done += len(cases)
+            if log:
+                log(f"pairs {done}/{len(seeds)}  waiting for host cases {t_wait:.1f} s  gpu {t_gpu:.1f} s")
+    finally:
+        ex.shutdown(cancel_futures=True)
+        if rec is not None:
+            rec.close()
+    return X, Y, dict(host_wait_s=t_wait, gpu_s=t_gpu)
+
+
+def train(cnn: CNN, X, Y, epochs: int, batch: int, lr: float, seed: int = 0, log=None,
+          lr_final: Optional[float] = None):
+    """Adam on minibatches of the pairs (X, Y: [N][n][n] device tensors),
+    shuffled per epoch by a seeded generator; the step size is `lr`, or, with
+    `lr_final`, decays from `lr` to `lr_final` on a cosine over all steps.
+    Returns the mean loss per epoch."""
+    import math
+
+    torch = _torch()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    N = X.shape[0]
+    xb = torch.empty((batch,) + tuple(X.shape[1:]), device=X.device)
+    yb = torch.empty_like(xb)
+    hist = []
+    per_epoch = max(1, N // batch)
+    total = epochs * per_epoch
+    step = 0
+    for ep in range(epochs):
+        order = rng.permutation(N)
+        tot, cnt = 0.0, 0
+        for b0 in range(0, N - batch + 1, batch):
+            idx = torch.from_numpy(order[b0:b0 + batch].astype(np.int64)).to(X.device)
+            torch.index_select(X, 0, idx, out=xb)
+            torch.index_select(Y, 0, idx, out=yb)
+            rate = lr
+            if lr_final is not None:
+                rate = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / max(1, total - 1)))
+            tot += cnn.train_step(xb, yb, rate)
+            step += 1
+            cnt += 1
+        hist.append(tot / max(cnt, 1))
+        if log:
+            log(f"epoch {ep + 1}/{epochs}  loss {hist[-1]:.6g}")
+    return hist
+
+
+def infer(cnn: CNN, X, out=None, stream=None):
+    """Warm-start images for the FBP images X ([N][n][n]), in chunks of the
+    network's batch size."""
+    torch = _torch()
+    out = torch.empty_like(X) if out is None else out
+    for b0 in range(0, X.shape[0], cnn.batch_max):
+        cnn.forward(X[b0:b0 + cnn.batch_max], out=out[b0:b0 + cnn.batch_max], stream=stream)
+    return out
+
+
+def evaluate(cnn: CNN, cases, Ks, device, width: int = 48, n_plain: int = N_ITER_TARGET, warm_opts=None,
+             keep_images: int = 0, truth=None):
+    """Compare, per case, the plain form (FBP start, `n_plain` sub-iterations)
+    with FBP start + K and network start + K sub-iterations (K in Ks, and the
+    start images themselves at K = 0). Objective Psi from ``mvct_objective``
+    (FP64 reduction on the GPU); image relative L2 against the plain result and,
+    when `truth` (list of images) is given, against the phantom.
+    `warm_opts`: loop options for the network-started runs (e.g. lambda0).
+    Returns a list of dicts; the first `keep_images` carry the images on the host."""
+    torch = _torch()
+    warm_opts = dict(warm_opts or {})
+    g = cases[0].geom
+    rec = StackReconstructor(g, cases[0].n_subsets, min(width, len(cases)), device)
+    out = []
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+    try:
+        for c0 in range(0, len(cases), rec.width):
+            ch = cases[c0:c0 + rec.width]
+            m = len(ch)
+            rec.load(ch)
+            fb = torch.stack([rec.fbp(k, torch.empty((g.n, g.n), device=device)) for k in range(m)])
+            cn = infer(cnn, fb)
+            betas = [c.beta for c in ch]
+            psi = lambda k, img: float(rec.plans[0].objective(img, rec.p[k], rec.w[k], ch[k].beta,
+                                                              ch[k].tv_eps).item())
+            res = [dict(seed=c.seed) for c in ch]
+            imgs = {}
+            plain = [t.clone() for t in rec.run(m, betas, list(fb), n_plain)]
+            for k in range(m):
+                res[k]["psi_plain"] = psi(k, plain[k])
+                res[k]["psi_fbp_K0"] = psi(k, fb[k])
+                res[k]["psi_cnn_K0"] = psi(k, cn[k])
+                res[k]["rel_plain_fbp_K0"] = rel(fb[k], plain[k])
+                res[k]["rel_plain_cnn_K0"] = rel(cn[k], plain[k])
+                imgs[(k, "plain")] = plain[k]
+            for K in Ks:
+                for name, starts, opts in (("fbp", fb, {}), ("cnn", cn, warm_opts)):
+                    r = rec.run(m, betas, list(starts), K, **opts)
+                    for k in range(m):
+                        res[k][f"psi_{name}_K{K}"] = psi(k, r[k])
+                        res[k][f"rel_plain_{name}_K{K}"] = rel(r[k], plain[k])
+                        if truth is not None:
+                            t = torch.from_numpy(np.asarray(truth[c0 + k], dtype=np.float32)).to(device)
+                            res[k][f"rel_truth_{name}_K{K}"] = rel(r[k], t)
+                        imgs[(k, f"{name}_K{K}")] = r[k].clone()
+            for k in range(m):
+                if c0 + k < keep_images:
+                    res[k]["images"] = {key[1]: v.cpu().numpy() for key, v in imgs.items() if key[0] == k}
+                    res[k]["images"]["fbp_K0"] = fb[k].cpu().numpy()
+                    res[k]["images"]["cnn_K0"] = cn[k].cpu().numpy()
+            out += res
+    finally:
+        rec.close()
+    return out
+
+
+def summarize(results, Ks, tol: float = 1e-3):
+    """Per start and K: the median / worst relative objective gap to the plain
+    form, (Psi - Psi_plain) / Psi_plain, and the fraction of cases within `tol`."""
+    s = {}
+    for name in ("fbp", "cnn"):
+        for K in [0] + list(Ks):
+            gap = np.array([(r[f"psi_{name}_K{K}"] - r["psi_plain"]) / r["psi_plain"] for r in results])
+            rl = np.array([r[f"rel_plain_{name}_K{K}"] for r in results])
+            s[f"{name}_K{K}"] = dict(gap_median=float(np.median(gap)), gap_max=float(gap.max()),
+                                     within_tol=float(np.mean(gap <= tol)), rel_l2_plain_median=float(np.median(rl)))
+    return s
+
+
+def weights_path() -> str:
+    import os
+
+    return os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart_512.npy")
+
+
+def load_weights(path: Optional[str] = None) -> np.ndarray:
+    p = np.load(path or weights_path())
+    if p.shape != (PARAM_COUNT,) or p.dtype != np.float32:
+        raise ValueError("warm-start weights have the wrong layout")
+    return p
+
+
+def _main(argv=None):
+    import argparse
+    import json
+    import os
+    import sys
+    import time
+
+    ap = argparse.ArgumentParser(description="train the warm-start network on pairs the method generates")
+    ap.add_argument("--pairs", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=20)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--lr-final", type=float, default=None, help="cosine decay of the step size to this value")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--width", type=int, default=96, help="slices per batched reconstruction")
+    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--out", default=weights_path())
+    args = ap.parse_args(argv)
+    torch = _torch()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    log = lambda s: print(s, file=sys.stderr, flush=True)
+    t0 = time.perf_counter()
+    X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width, workers=args.workers,
+                          log=log)
+    t1 = time.perf_counter()
+    cnn = CNN(args.batch, X.shape[1], X.shape[2], init_params(args.seed))
+    hist = train(cnn, X, Y, args.epochs, args.batch, args.lr, args.seed, log, lr_final=args.lr_final)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    params = cnn.params()
+    cnn.close()
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.save(args.out, params)
+    rec = dict(pairs=args.pairs, train_seeds=[TRAIN_SEED0, TRAIN_SEED0 + args.pairs - 1], epochs=args.epochs,
+               batch=args.batch, lr=args.lr, lr_final=args.lr_final, seed=args.seed, target_iterations=N_ITER_TARGET,
+               epoch_loss=hist, pair_generation_s=t1 - t0, pair_timing=tp, training_s=t2 - t1,
+               steps=args.epochs * (args.pairs // args.batch))
+    with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
+    return 0
+
+
+if __name__ == "__main__":
+    import sys
+
+    sys.exit(_main())

@@ -14,3 +14,14 @@ def full_case_recon(seed: int, beta: float, n_iter: int):
     c = ph.make_case("full", seed, beta=beta, n_iter=n_iter)
     r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, beta, n_iter)
     return r["image"].astype(np.float64), r["phi"], r["lam"]
+
+
+def full_case_objective(seed: int, img):
+    """FP64 oracle objective of an image for the seeded full-size case."""
+    c = ph.make_case("full", seed)
+    return oracle.objective(c.geom, np.asarray(img, dtype=np.float64), c.p, c.w, c.beta, c.tv_eps)
+
+
+def case_and_truth(seed: int, kind: str = "full"):
+    c = ph.make_case(kind, seed)
+    return c, c.truth(2)
