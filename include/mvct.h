@@ -93,7 +93,19 @@ typedef struct mvct_recon_opts {
     double barrier_timeout_ms;     /* grid-barrier wait limit (2000) */
     int32_t debug_unreachable_barrier; /* test knob: the first barrier can never complete */
     int32_t data_term;             /* MVCT_DATA_WLS (0, default) or MVCT_DATA_POISSON (1) */
+    int32_t storage;               /* MVCT_STORAGE_F32 (0, default), _BF16 (1) or _F16 (2); mvct_recon only */
 } mvct_recon_opts;
+
+/* Storage precision of mvct_recon. F32: every buffer FP32. BF16 / F16: the copies
+ * of the iterate that the reprojection reads (the image and its transpose) and
+ * the measured p and w are stored in that 16-bit type (round to nearest) and
+ * widened to FP32 on load; the iterate itself stays FP32 (the update of Eq. 3
+ * is applied to the FP32 image, then rounded into the 16-bit copies). All
+ * arithmetic is FP32 (projection, backprojection, TV, update); Phi and the
+ * objective are summed in FP64. mvct_batch_* accept F32 only. */
+#define MVCT_STORAGE_F32 0
+#define MVCT_STORAGE_BF16 1
+#define MVCT_STORAGE_F16 2
 
 /* Data terms of mvct_recon (Sec. 2: Poisson photon statistics).
  * WLS:     1/2 sum w_i ([A mu]_i - p_i)^2, the quadratic (log-domain) approximation.

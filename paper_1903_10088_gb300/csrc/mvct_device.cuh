@@ -13,8 +13,12 @@
 //                     wait (global timer limit plus a spin cap).
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 namespace mvct {
 
@@ -45,6 +49,30 @@ __device__ __forceinline__ float ldf(const float *p)
 {
     if constexpr (RO) return __ldg(p);
     else return *p;
+}
+
+// Load one stored element (FP32, BF16 or FP16) widened to FP32.
+template <bool RO, typename TS>
+__device__ __forceinline__ float ldv(const TS *p)
+{
+    if constexpr (std::is_same<TS, float>::value) {
+        return ldf<RO>(p);
+    } else if constexpr (std::is_same<TS, __nv_bfloat16>::value) {
+        if constexpr (RO) return __bfloat162float(__ldg(p));
+        else return __bfloat162float(*p);
+    } else {
+        if constexpr (RO) return __half2float(__ldg(p));
+        else return __half2float(*p);
+    }
+}
+
+// Round an FP32 value to the storage type (round to nearest even).
+template <typename TS>
+__device__ __forceinline__ TS to_storage(float v)
+{
+    if constexpr (std::is_same<TS, float>::value) return v;
+    else if constexpr (std::is_same<TS, __nv_bfloat16>::value) return __float2bfloat16_rn(v);
+    else return __float2half_rn(v);
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -83,13 +111,14 @@ constexpr int kPadRows = 2;
 // the same value). img is row-major; imgT is its transpose: a y-driven ray walks
 // the rows of img, which are the columns of imgT, so reading imgT keeps the
 // warp's accesses contiguous. RO selects read-only-cache loads (only legal when
-// the image is not written during the kernel).
-template <bool RO>
-__device__ __forceinline__ float joseph_warp(const float *img, const float *imgT, int n, float pc,
+// the image is not written during the kernel). TS is the stored element type
+// (FP32, BF16 or FP16); taps are widened to FP32 and the sum is FP32.
+template <bool RO, typename TS = float>
+__device__ __forceinline__ float joseph_warp(const TS *img, const TS *imgT, int n, float pc,
                                              float4 r, int lane)
 {
     // img / imgT point at row 0 of zero-row-padded buffers (see kPadRows)
-    const float *src = (r.w > 0.5f) ? img : imgT;
+    const TS *src = (r.w > 0.5f) ? img : imgT;
     const float uc = r.x, m = r.y;
     // Samples whose taps can fall inside the image: u(p) in (-1, n), widened by
     // one sample (taps outside land on the zero rows).
@@ -114,9 +143,9 @@ __device__ __forceinline__ float joseph_warp(const float *img, const float *imgT
         for (int q = 0; q < U; ++q) {
             const float u = fmaf(m, pf + (float)(q * 32), uc);
             const int i0 = min(max(floor_frac(u, f[q]), rmin), rmax);
-            const float *t = src + (i0 * n + p + q * 32);
-            ta[q] = ldf<RO>(t);
-            tb[q] = ldf<RO>(t + n);
+            const TS *t = src + (i0 * n + p + q * 32);
+            ta[q] = ldv<RO>(t);
+            tb[q] = ldv<RO>(t + n);
         }
 #pragma unroll
         for (int q = 0; q < U; ++q) acc += fmaf(f[q], tb[q] - ta[q], ta[q]);
@@ -124,8 +153,8 @@ __device__ __forceinline__ float joseph_warp(const float *img, const float *imgT
     for (; p <= p_hi; p += 32, pf += 32.f) {
         float f;
         const int i0 = min(max(floor_frac(fmaf(m, pf, uc), f), rmin), rmax);
-        const float *t = src + (i0 * n + p);
-        const float a = ldf<RO>(t), b = ldf<RO>(t + n);
+        const TS *t = src + (i0 * n + p);
+        const float a = ldv<RO>(t), b = ldv<RO>(t + n);
         acc += fmaf(f, b - a, a);
     }
     return warp_sum(acc) * r.z;

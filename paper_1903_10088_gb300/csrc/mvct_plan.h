@@ -19,6 +19,11 @@ struct SliceDesc {
     const float *D;           // surrogate diagonal [n][n]
     float *mu0, *mu1;         // row 0 of the padded ping-pong images
     float *muT0, *muT1;       // and of their transposes
+    // 16-bit storage (mvct_recon_opts.storage): row 0 of the padded 16-bit copies
+    // of the ping-pong images and transposes that the reprojection reads, and the
+    // 16-bit p and w (unused with FP32 storage)
+    void *hm0, *hm1, *hmT0, *hmT1;
+    const void *hp, *hw;
     float4 *e4;               // [Vs][C] per-ray (u_c, m, prescaled residual, flag)
     float *tile_part;         // [n_tiles][groups-1][32*32] partial tiles
     unsigned int *tile_flag;  // [n_tiles][groups-1] publication stamps
@@ -91,6 +96,10 @@ struct mvct_plan_s {
     int *d_block_group = nullptr;       // [recon_grid] zeros
     unsigned int *d_count = nullptr;    // group barrier counter
     bool in_batch = false;              // owned by a batch (its scratch is in use there)
+    // 16-bit storage buffers (allocated on first use): padded ping-pong image
+    // copies and transposes, p and w
+    void *pad16[4] = {nullptr, nullptr, nullptr, nullptr};
+    void *p16 = nullptr, *w16 = nullptr;
     float *fbp_g = nullptr;             // [2C-1] fan-beam ramp g(k a)
     float *fbp_cos = nullptr;           // [C] D cos(gamma_c)
     float fbp_a = 0.f;                  // channel pitch (rad)

@@ -65,7 +65,7 @@ struct LoopShared {
 // All n_iter sub-iterations of one slice by the blocks of one group (lb = this
 // block's index in the group, bk = the group's barrier count so far). Returns
 // false if the block must leave the kernel (a wait gave up).
-template <class SD, class GD>
+template <typename TS, class SD, class GD>
 __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const LoopArgs &a, int lb,
                                           unsigned int &bk, LoopShared &sh, bool timer,
                                           unsigned long long &t_f, unsigned long long &t_b,
@@ -86,8 +86,11 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
     const long long n0 = st->n_done;
     const int Rs = g.Vs * g.C;
     const float S_f = (float)g.S;
+    constexpr bool F32 = std::is_same<TS, float>::value;
     const float4 *rays = sd.rays;
-    const float *pp = sd.p, *ww = sd.w;
+    // measured p and w as stored (FP32, or the 16-bit copies)
+    const TS *pp = F32 ? (const TS *)sd.p : (const TS *)sd.hp;
+    const TS *ww = F32 ? (const TS *)sd.w : (const TS *)sd.hw;
     float4 *e4 = sd.e4;
     
 
@@ -99,6 +102,12 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         const float *curT = odd ? sd.muT1 : sd.muT0;
         float *nxt = odd ? sd.mu0 : sd.mu1;
         float *nxtT = odd ? sd.muT0 : sd.muT1;
+        // the copies the reprojection reads: the FP32 images themselves, or their
+        // 16-bit copies (the FP32 iterate is the master for TV and the update)
+        const TS *pcur = F32 ? (const TS *)cur : (const TS *)(odd ? sd.hm1 : sd.hm0);
+        const TS *pcurT = F32 ? (const TS *)curT : (const TS *)(odd ? sd.hmT1 : sd.hmT0);
+        TS *pnxt = F32 ? (TS *)nxt : (TS *)(odd ? sd.hm0 : sd.hm1);
+        TS *pnxtT = F32 ? (TS *)nxtT : (TS *)(odd ? sd.hmT0 : sd.hmT1);
         const unsigned int stamp = (unsigned int)it + 1u;
 
         // ---- phase F: reprojection, residual, square difference ---------
@@ -113,8 +122,8 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 const size_t rv = (size_t)(s + k * g.S) * g.C + (gw0 - k * g.C);
                 r_nx = __ldg(&rays[rv]);
                 if (lane == 0) {
-                    p_nx = __ldg(pp + rv);
-                    w_nx = __ldg(ww + rv);
+                    p_nx = ldv<true>(pp + rv);
+                    w_nx = ldv<true>(ww + rv);
                 }
             }
             for (int ray = gw0; ray < Rs; ray += GW) {
@@ -126,11 +135,11 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                     const size_t rv = (size_t)(s + k * g.S) * g.C + (nray - k * g.C);
                     r_nx = __ldg(&rays[rv]);
                     if (lane == 0) {
-                        p_nx = __ldg(pp + rv);
-                        w_nx = __ldg(ww + rv);
+                        p_nx = ldv<true>(pp + rv);
+                        w_nx = ldv<true>(ww + rv);
                     }
                 }
-                const float q_ray = joseph_warp<false>(cur, curT, g.n, g.pc, r, lane);
+                const float q_ray = joseph_warp<false, TS>(pcur, pcurT, g.n, g.pc, r, lane);
                 if (lane == 0) {
                     const float res = q_ray - pv;
                     const float ev = a.poisson ? wv - expf(-q_ray) : wv * res;
@@ -292,6 +301,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                         nm = fmaxf(0.f, m - tau * d * fmaf(S_f, gs, beta * tg));
                     }
                     nxt[r] = nm;
+                    if constexpr (!F32) pnxt[r] = to_storage<TS>(nm);
                 }
                 part_val[u] = nm;
             }
@@ -307,7 +317,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 const int idx = threadIdx.x + u * kThreads;
                 const int jj = idx >> 5, ii = idx & 31; // transposed: row of muT = column j
                 const int i = i_lo + ii, j = j_lo + jj;
-                if (i < g.n && j < g.n) nxtT[(size_t)j * g.n + i] = tile[ii * kAccStride + jj];
+                if (i < g.n && j < g.n) pnxtT[(size_t)j * g.n + i] = to_storage<TS>(tile[ii * kAccStride + jj]);
             }
             __syncthreads(); // tile (sh.acc[0]) is zeroed by the next item
         }
@@ -337,7 +347,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
 // The loop kernel: BATCH = false reads the one slice and group from the kernel
 // parameters; BATCH = true reads each block's group and its slices from global
 // descriptor arrays (copied to shared memory).
-template <bool BATCH>
+template <bool BATCH, typename TS = float>
 __global__ void __launch_bounds__(kThreads, 4) k_recon(LoopArgs a)
 {
     __shared__ LoopShared sh;
@@ -357,15 +367,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_recon(LoopArgs a)
                 for (int k = threadIdx.x; k < (int)(sizeof(SliceDesc) / sizeof(int)); k += kThreads) dst[k] = src[k];
             }
             __syncthreads();
-            if (!run_slice(sh.sd, sh.grp, a, lb, bk, sh, timer && si == 0, t_f, t_b, t_mark)) return;
+            if (!run_slice<TS>(sh.sd, sh.grp, a, lb, bk, sh, timer && si == 0, t_f, t_b, t_mark)) return;
         }
     } else {
-        if (!run_slice(a.one, a.one_group, a, (int)blockIdx.x, bk, sh, timer, t_f, t_b, t_mark)) return;
+        if (!run_slice<TS>(a.one, a.one_group, a, (int)blockIdx.x, bk, sh, timer, t_f, t_b, t_mark)) return;
     }
     if (timer) {
         a.phase_ns[0] = t_f;
         a.phase_ns[1] = t_b;
     }
+}
+
+// dst[k] = src[k] rounded to the 16-bit storage type, k < count.
+template <typename TS>
+__global__ void k_to_storage(const float *__restrict__ src, TS *__restrict__ dst, size_t count)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = to_storage<TS>(src[k]);
 }
 
 // Fresh loop state for `count` slices.
@@ -469,6 +487,8 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         return mvct_fail(MVCT_EINVAL, "mvct_recon: invalid options");
     if (o.state && (o.state->n_done < 0 || (o.state->n_done > 0 && !o.init_from_input)))
         return mvct_fail(MVCT_EINVAL, "mvct_recon: resuming (state->n_done > 0) needs init_from_input = 1");
+    if (o.storage != MVCT_STORAGE_F32 && o.storage != MVCT_STORAGE_BF16 && o.storage != MVCT_STORAGE_F16)
+        return mvct_fail(MVCT_EINVAL, "mvct_recon: storage %d unknown", o.storage);
     if (P->recon_grid <= 0) return mvct_fail(MVCT_ELAUNCH, "mvct_recon: loop kernel has no occupancy");
 
     if (P->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_recon: plan belongs to a batch");
@@ -502,6 +522,28 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     float *mu_a = pad_row0(P->pad[0], n), *mu_b = pad_row0(P->pad[1], n);
     float *muT_a = pad_row0(P->pad[2], n), *muT_b = pad_row0(P->pad[3], n);
 
+    const bool half = o.storage != MVCT_STORAGE_F32;
+    if (half && !P->p16) {
+        // 16-bit copies, 2 bytes per element; zeroed so the pad rows read as 0
+        const size_t R = (size_t)g.V * g.C;
+        bool ok = true;
+        for (int k = 0; k < 4; ++k) ok = ok && cudaMalloc(&P->pad16[k], 2 * pad_floats(n)) == cudaSuccess;
+        ok = ok && cudaMalloc(&P->p16, 2 * R) == cudaSuccess && cudaMalloc(&P->w16, 2 * R) == cudaSuccess;
+        for (int k = 0; k < 4 && ok; ++k) ok = cudaMemset(P->pad16[k], 0, 2 * pad_floats(n)) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            for (auto &b : P->pad16) {
+                cudaFree(b);
+                b = nullptr;
+            }
+            cudaFree(P->p16);
+            cudaFree(P->w16);
+            P->p16 = P->w16 = nullptr;
+            return mvct_fail(MVCT_ENOMEM, "mvct_recon: cannot allocate the 16-bit storage");
+        }
+    }
+    auto h_row0 = [&](int k) { return (void *)((char *)P->pad16[k] + 2 * (size_t)kPadRows * n); };
+
     SliceDesc sd;
     std::memset(&sd, 0, sizeof(sd));
     sd.g = g;
@@ -514,6 +556,14 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     sd.mu1 = mu_b;
     sd.muT0 = muT_a;
     sd.muT1 = muT_b;
+    if (half) {
+        sd.hm0 = h_row0(0);
+        sd.hm1 = h_row0(1);
+        sd.hmT0 = h_row0(2);
+        sd.hmT1 = h_row0(3);
+        sd.hp = P->p16;
+        sd.hw = P->w16;
+    }
     sd.e4 = P->e4;
     sd.tile_part = P->tile_part;
     sd.tile_flag = P->tile_flag;
@@ -544,6 +594,23 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     const double cb = beta * 8.0 / std::sqrt(o.tv_eps);
     CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0,
                          d_img_inout, mu_a, muT_a, st));
+    if (half) {
+        // the 16-bit copies of p, w and of the start image and its transpose
+        const size_t R = (size_t)g.V * g.C;
+        const int cg = P->num_sms * 8;
+        if (o.storage == MVCT_STORAGE_BF16) {
+            k_to_storage<<<cg, kThreads, 0, st>>>(d_sino, (__nv_bfloat16 *)P->p16, R);
+            k_to_storage<<<cg, kThreads, 0, st>>>(d_weights, (__nv_bfloat16 *)P->w16, R);
+            k_to_storage<<<cg, kThreads, 0, st>>>(P->pad[0], (__nv_bfloat16 *)P->pad16[0], pad_floats(n));
+            k_to_storage<<<cg, kThreads, 0, st>>>(P->pad[2], (__nv_bfloat16 *)P->pad16[2], pad_floats(n));
+        } else {
+            k_to_storage<<<cg, kThreads, 0, st>>>(d_sino, (__half *)P->p16, R);
+            k_to_storage<<<cg, kThreads, 0, st>>>(d_weights, (__half *)P->w16, R);
+            k_to_storage<<<cg, kThreads, 0, st>>>(P->pad[0], (__half *)P->pad16[0], pad_floats(n));
+            k_to_storage<<<cg, kThreads, 0, st>>>(P->pad[2], (__half *)P->pad16[2], pad_floats(n));
+        }
+        CK(cudaGetLastError());
+    }
     CK(cudaEventRecord(ev.e[1], st));
 
     if (n_iter > 0) {
@@ -565,8 +632,10 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
         a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
         void *args[] = {&a};
-        cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon<false>, dim3(P->recon_grid),
-                                                     dim3(kThreads), args, 0, st);
+        const void *kern = o.storage == MVCT_STORAGE_BF16  ? (const void *)k_recon<false, __nv_bfloat16>
+                           : o.storage == MVCT_STORAGE_F16 ? (const void *)k_recon<false, __half>
+                                                           : (const void *)k_recon<false, float>;
+        cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(P->recon_grid), dim3(kThreads), args, 0, st);
         if (le == cudaErrorCooperativeLaunchTooLarge)
             return mvct_fail(MVCT_ELAUNCH, "mvct_recon: %d blocks cannot be co-resident", P->recon_grid);
         if (le != cudaSuccess)
@@ -790,6 +859,7 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
         !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
         (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
         return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: invalid options");
+    if (o.storage != MVCT_STORAGE_F32) return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: only FP32 storage");
     for (int i = 0; i < b->count; ++i) {
         if (!d_sinos[i] || !d_weights[i] || !d_imgs[i])
             return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: null device pointer for slice %d", i);

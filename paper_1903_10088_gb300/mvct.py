@@ -73,6 +73,7 @@ class ReconOpts(ctypes.Structure):
         ("barrier_timeout_ms", ctypes.c_double),
         ("debug_unreachable_barrier", ctypes.c_int32),
         ("data_term", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
     ]
 
 
@@ -173,6 +174,9 @@ def geometry(g) -> Geometry:
                     g.fan_angle_rad, g.channel_offset)
 
 
+STORAGE = {"f32": 0, "bf16": 1, "f16": 2}   # mvct_recon_opts.storage (MVCT_STORAGE_*)
+
+
 @dataclass
 class ReconResult:
     phi: np.ndarray
@@ -271,6 +275,8 @@ class Plan:
             img = torch.zeros((self.n, self.n), device=p.device, dtype=torch.float32)
         o = ReconOpts()
         lib().mvct_recon_opts_init(ctypes.byref(o))
+        if isinstance(opts.get("storage"), str):
+            opts = dict(opts, storage=STORAGE[opts["storage"]])
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")

@@ -25,3 +25,14 @@ def full_case_objective(seed: int, img):
 def case_and_truth(seed: int, kind: str = "full"):
     c = ph.make_case(kind, seed)
     return c, c.truth(2)
+
+
+def full_case_recon_checkpoints(seed: int, beta: float, checkpoints):
+    """Oracle images and lambda sequences after each of `checkpoints` sub-iterations
+    (separate runs from the same start)."""
+    c = ph.make_case("full", seed, beta=beta)
+    out = {}
+    for n in checkpoints:
+        r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, beta, n)
+        out[n] = (r["image"].astype(np.float64), r["lam"])
+    return out

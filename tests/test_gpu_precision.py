@@ -1,0 +1,91 @@
+"""16-bit storage (mvct_recon_opts.storage = BF16 / FP16): the reprojection reads
+16-bit copies of the iterate and of p and w, all arithmetic stays FP32 and the
+iterate itself FP32. Errors against the FP64 oracle, with the oracle's lambda
+sequence replayed (arithmetic only) and with the loop's own adaptive lambda,
+beside the FP32 run; at the full size after 50, 100 and 500 sub-iterations."""
+import concurrent.futures as cf
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1903_10088_gb300 import phantom as ph
+
+pytestmark = pytest.mark.gpu
+
+STORAGES = ("f32", "bf16", "f16")
+# relative L2 bounds against the oracle (lambda replayed). Full size, measured on
+# GB300 after 50 / 100 / 500 sub-iterations: FP32 6.4e-7 / 7.1e-7 / 1.4e-6,
+# FP16 1.7e-4 / 3.0e-4 / 7.0e-4, BF16 1.4e-3 / 2.4e-3 / 5.6e-3.
+BOUND_SMALL = {"f32": 1e-4, "bf16": 2e-2, "f16": 3e-3}
+BOUND_FULL = {"f32": 1e-4, "bf16": 1.5e-2, "f16": 2e-3}
+
+
+def rel(a, b):
+    a, b = np.ravel(np.asarray(a, dtype=np.float64)), np.ravel(np.asarray(b, dtype=np.float64))
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def mvct():
+    from paper_1903_10088_gb300 import build, mvct
+
+    build.build()
+    mvct.lib()
+    return mvct
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def gpu_recon(mvct, c, n_iter, storage, sched=None):
+    with mvct.Plan(c.geom, c.n_subsets) as plan:
+        img, res = plan.recon(cuda(c.p), cuda(c.w), c.beta, n_iter, lambda_schedule=sched, storage=storage)
+        torch.cuda.synchronize()
+        return img.double().cpu().numpy(), res
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_storage_small(mvct, seed):
+    c = ph.make_case("small", seed)
+    ref = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, c.n_iter)
+    errs = {}
+    for stg in STORAGES:
+        img, _ = gpu_recon(mvct, c, c.n_iter, stg, sched=ref["lam"])
+        errs[stg] = rel(img, ref["image"])
+        assert errs[stg] < BOUND_SMALL[stg], (stg, errs)
+    # the 16-bit runs really ran in 16 bits
+    assert errs["bf16"] > errs["f16"] > errs["f32"]
+    # adaptive lambda: same bounds unless a decision flipped (then report, no bound)
+    for stg in STORAGES:
+        img, res = gpu_recon(mvct, c, c.n_iter, stg)
+        if np.array_equal(res.lam, ref["lam"]):
+            assert rel(img, ref["image"]) < BOUND_SMALL[stg]
+
+
+def test_storage_full_size_error_table(mvct, capsys):
+    """512^2, 800 x 738, S = 20, beta = 1e-3: relative L2 error against the oracle
+    after 50, 100 and 500 sub-iterations for FP32, BF16 and FP16 storage."""
+    import oracle_jobs
+
+    seed, beta, cps = 100, 1e-3, (50, 100, 500)
+    with cf.ProcessPoolExecutor(3, mp_context=mp.get_context("spawn")) as ex:
+        futs = {n: ex.submit(oracle_jobs.full_case_recon_checkpoints, seed, beta, (n,)) for n in cps}
+        c = ph.make_case("full", seed, beta=beta)
+        gpu = {(stg, n): gpu_recon(mvct, c, n, stg)[0] for stg in STORAGES for n in cps}
+        ref = {n: futs[n].result()[n] for n in cps}
+    table = {}
+    for n in cps:
+        for stg in STORAGES:
+            img_r, _ = gpu_recon(mvct, c, n, stg, sched=ref[n][1])
+            table[(stg, n)] = (rel(img_r, ref[n][0]), rel(gpu[(stg, n)], ref[n][0]))
+    with capsys.disabled():
+        print("\nstorage  n    rel L2 (lambda replayed)  rel L2 (adaptive)")
+        for (stg, n), (e_r, e_a) in table.items():
+            print(f"{stg:6s} {n:4d}   {e_r:.3e}                {e_a:.3e}")
+    for n in cps:
+        for stg in STORAGES:
+            assert table[(stg, n)][0] < BOUND_FULL[stg], (stg, n, table[(stg, n)])
