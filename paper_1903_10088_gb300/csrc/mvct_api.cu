@@ -114,7 +114,7 @@ void build_tables(const mvct_geometry &g, int S, std::vector<float4> &rays, std:
 void free_plan(mvct_plan_s *P)
 {
     if (!P) return;
-    void *ptrs[] = {P->rays, P->views, P->a1t, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
+    void *ptrs[] = {P->rays, P->views, P->a1t, P->a1, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
                     P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
                     P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched,
                     P->d_slice, P->d_group, P->d_block_group, P->d_count, P->fbp_g, P->fbp_cos,
@@ -163,6 +163,7 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     bool ok = cudaMalloc(&P->rays, R * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->views, g->n_views * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->a1t, nn * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&P->a1, R * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->pad[0], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->pad[1], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->pad[2], pad_floats(g->n) * sizeof(float)) == cudaSuccess &&
@@ -198,6 +199,10 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     if (e == cudaSuccess) e = launch_fill(pad_row0(P->pad_ones, g->n), nn, 1.f, st);
     if (e == cudaSuccess) e = launch_fill(P->sino_tmp, R, 1.f, st);
     if (e == cudaSuccess) e = launch_back(P, P->sino_tmp, P->a1t, -1, st); // A^T 1
+    if (e == cudaSuccess) {
+        const float *ones = pad_row0(P->pad_ones, g->n);
+        e = launch_forward(P, ones, ones, P->a1, -1, nullptr, nullptr, nullptr, st); // A 1
+    }
     if (e == cudaSuccess) e = cudaMemset(P->bar, 0, sizeof(Barrier));
     if (e == cudaSuccess) e = cudaMemset(P->d_block_group, 0, sizeof(int) * std::max(1, P->recon_grid));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

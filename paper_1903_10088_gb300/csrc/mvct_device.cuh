@@ -395,8 +395,10 @@ __device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gp
 // nblocks blocks that share `count`: each block adds one arrival with release
 // semantics and polls (relaxed) until the counter reaches (k+1)*nblocks + extra,
 // then takes an acquire fence. extra > 0 makes the barrier unreachable (test
-// knob). Returns false in every thread of the block if the wait hit timeout_ns
-// or spin_cap, or if any block has set *err; the caller then leaves the kernel.
+// knob). The poll is tight; every 64th poll also reads *err and the global
+// timer, and after 4096 polls each of those adds a short sleep. Returns false in
+// every thread of the block if the wait hit timeout_ns or spin_cap, or if any
+// block has set *err; the caller then leaves the kernel.
 __device__ __forceinline__ bool group_sync(unsigned int *count, int *err, unsigned int k,
                                            unsigned int nblocks, unsigned int extra,
                                            unsigned long long timeout_ns, unsigned long long spin_cap)
@@ -409,15 +411,21 @@ __device__ __forceinline__ bool group_sync(unsigned int *count, int *err, unsign
         add_release(count, 1u);
         unsigned long long spins = 0, t0 = 0;
         while ((int)(ld_relaxed(count) - target) < 0) {
-            if (*(volatile int *)err) { ok = 0; break; }
             ++spins;
-            if (spins == 64) t0 = global_ns();
-            if (spins > spin_cap || (spins > 64 && (spins & 15u) == 0 && global_ns() - t0 > timeout_ns)) {
-                atomicExch(err, 1);
-                ok = 0;
-                break;
+            if ((spins & 63u) == 0) {
+                if (*(volatile int *)err) {
+                    ok = 0;
+                    break;
+                }
+                if (spins == 64) {
+                    t0 = global_ns();
+                } else if (spins > spin_cap || global_ns() - t0 > timeout_ns) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                if (spins >= 4096) __nanosleep(64);
             }
-            if (spins > 16) __nanosleep(20);
         }
         fence_acquire();
         if (*(volatile int *)err) ok = 0;

@@ -61,6 +61,21 @@ k_forward(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img,
     }
 }
 
+// Set-up product w .* (A 1) from the plan's cached A 1 (the same FP32 product
+// k_forward forms with mul = w), with the input check of p and w.
+__global__ void __launch_bounds__(kThreads)
+k_weight_a1(const float *__restrict__ a1, const float *__restrict__ w, const float *__restrict__ p,
+            float *__restrict__ out, size_t count, int *data_err)
+{
+    bool bad = false;
+    for (size_t k = (size_t)blockIdx.x * kThreads + threadIdx.x; k < count; k += (size_t)gridDim.x * kThreads) {
+        const float wv = __ldg(w + k), pv = __ldg(p + k);
+        bad |= !isfinite(pv) || !isfinite(wv) || wv < 0.f;
+        out[k] = __ldg(a1 + k) * wv;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicExch(data_err, 1);
+}
+
 // Per-block FP64 sum of w * (A img - p)^2 over all views (one warp per ray).
 __global__ void __launch_bounds__(kThreads)
 k_residual(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img,
@@ -236,6 +251,15 @@ cudaError_t launch_forward(const mvct_plan_s *P, const float *img, const float *
     const int rows = rows_of(P, subset);
     k_forward<<<ray_grid(P, (long long)rows * P->geo.C), kThreads, 0, st>>>(
         P->geo, P->rays, img, imgT, out, subset, rows, mul, check_p, data_err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weight_a1(const mvct_plan_s *P, const float *w, const float *p, float *out, int *data_err,
+                             cudaStream_t st)
+{
+    const size_t R = (size_t)P->geo.V * P->geo.C;
+    const int grid = (int)std::max<size_t>(1, std::min<size_t>((R + kThreads - 1) / kThreads, (size_t)P->num_sms * 8));
+    k_weight_a1<<<grid, kThreads, 0, st>>>(P->a1, w, p, out, R, data_err);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,7 @@ struct mvct_plan_s {
     float4 *rays = nullptr;     // [V*C] ray table (see mvct_device.cuh)
     float4 *views = nullptr;    // [V] source point and central direction
     float *a1t = nullptr;       // [n*n] A^T 1 over all views (support mask = a1t > 0)
+    float *a1 = nullptr;        // [V*C] A 1 (projection of the all-ones image), geometry only
     // Zero-row-padded images ((n + 2*kPadRows) rows of n floats; the pointers
     // below address the allocation, row 0 of the image is at + kPadRows*n):
     // pad[0], pad[1] the loop's ping-pong image, pad[2], pad[3] their transposes;
@@ -127,6 +128,8 @@ cudaError_t launch_tv(const mvct_plan_s *P, const float *img, float eps, float *
                       double *partials, cudaStream_t st);
 cudaError_t launch_tv_grid(int n, const float *img, float eps, float *grad, double *partials, int grid,
                            cudaStream_t st);
+cudaError_t launch_weight_a1(const mvct_plan_s *P, const float *w, const float *p, float *out, int *data_err,
+                             cudaStream_t st);
 cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float *imgT,
                             const float *p, const float *w, double *partials, cudaStream_t st);
 cudaError_t launch_final_sum(const double *a, int na, double ca, const double *b, int nb, double cb,

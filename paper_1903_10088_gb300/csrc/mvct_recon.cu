@@ -29,21 +29,25 @@
 
 namespace mvct {
 
-// Wait until flag == stamp (bounded like the group barrier). Thread 0 only.
+// Wait until flag == stamp (bounded like the group barrier: tight polls, every
+// 64th also reads *err and the timer, sleeps after 4096). Thread 0 only.
 __device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int stamp, int *err,
                                           unsigned long long timeout_ns, unsigned long long spin_cap)
 {
     if (ld_acquire(flag) == stamp) return true;
-    const unsigned long long t0 = global_ns();
-    unsigned long long spins = 0;
+    unsigned long long spins = 0, t0 = 0;
     while (ld_acquire(flag) != stamp) {
-        if (*(volatile int *)err) return false;
         ++spins;
-        if (spins > spin_cap || ((spins & 31u) == 0 && global_ns() - t0 > timeout_ns)) {
-            atomicExch(err, 1);
-            return false;
+        if ((spins & 63u) == 0) {
+            if (*(volatile int *)err) return false;
+            if (spins == 64) {
+                t0 = global_ns();
+            } else if (spins > spin_cap || global_ns() - t0 > timeout_ns) {
+                atomicExch(err, 1);
+                return false;
+            }
+            if (spins >= 4096) __nanosleep(64);
         }
-        __nanosleep(32);
     }
     return true;
 }
@@ -589,8 +593,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     Events ev;
     CK(cudaEventRecord(ev.e[0], st));
     // set-up (a0): w .* A1 over all views (and input validation), then D and mu0
-    const float *ones = pad_row0(P->pad_ones, n);
-    CK(launch_forward(P, ones, ones, P->sino_tmp, -1, d_weights, d_sino, &P->bar->data_err, st));
+    CK(launch_weight_a1(P, d_weights, d_sino, P->sino_tmp, &P->bar->data_err, st));
     const double cb = beta * 8.0 / std::sqrt(o.tv_eps);
     CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0,
                          d_img_inout, mu_a, muT_a, st));
@@ -930,9 +933,8 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
     for (int i = 0; i < b->count; ++i) {
         mvct_plan_s *P = b->plans[i];
         const int n = P->geo.n;
-        const float *ones = pad_row0(P->pad_ones, n);
         CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups, st));
-        CK(launch_forward(P, ones, ones, P->sino_tmp, -1, b->weights[i], b->sinos[i], &b->d_bar->data_err, st));
+        CK(launch_weight_a1(P, b->weights[i], b->sinos[i], P->sino_tmp, &b->d_bar->data_err, st));
         const double cb = b->betas[i] * 8.0 / std::sqrt(o.tv_eps);
         CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0, b->imgs[i],
                              pad_row0(P->pad[0], n), pad_row0(P->pad[2], n), st));

@@ -1,12 +1,14 @@
 """Per-operator timing of the C ABI on one GPU (CUDA events, warm caches).
 
     python -m paper_1903_10088_gb300.opbench [--n 512 --views 800 --channels 738 --subsets 20]
-                                             [--ops forward,back,tv,objective] [--reps 20]
+                                             [--ops forward,back,tv,objective,fbp,cnn] [--reps 20]
+                                             [--cnn-batch 16]
 
 Times mvct_forward / mvct_back on one subset (the per-sub-iteration work of the
-reconstruction loop) and on all views, mvct_tv_grad and mvct_objective, on
-seeded random inputs, and prints one JSON object. Also the driver for
-kernel-level profiler captures of the individual operators.
+reconstruction loop) and on all views, mvct_tv_grad, mvct_objective, mvct_fbp,
+and the warm-start network (forward, and one Adam training step, on a batch of
+--cnn-batch n x n images), on seeded random inputs, and prints one JSON object.
+Also the driver for kernel-level profiler captures of the individual operators.
 """
 from __future__ import annotations
 
@@ -39,8 +41,9 @@ def main(argv=None):
     ap.add_argument("--views", type=int, default=800)
     ap.add_argument("--channels", type=int, default=738)
     ap.add_argument("--subsets", type=int, default=20)
-    ap.add_argument("--ops", default="forward,back,tv,objective")
+    ap.add_argument("--ops", default="forward,back,tv,objective,fbp,cnn")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--cnn-batch", type=int, default=16)
     args = ap.parse_args(argv)
     g = ph.Geometry(n=args.n, n_views=args.views, n_channels=args.channels)
     rng = np.random.default_rng(0)
@@ -65,6 +68,23 @@ def main(argv=None):
             out["ms"]["tv_grad"] = timed(lambda: plan.tv_grad(img, 1e-6), args.reps)
         if "objective" in ops:
             out["ms"]["objective"] = timed(lambda: plan.objective(img, sino, w, 1e-3, 1e-6), args.reps)
+        if "fbp" in ops:
+            out["ms"]["fbp"] = timed(lambda: plan.fbp(sino, out=b), args.reps)
+    if "cnn" in ops:
+        from . import warmstart as ws
+
+        N = args.cnn_batch
+        x = torch.from_numpy(rng.uniform(0, 0.1, (N, g.n, g.n)).astype(np.float32)).cuda()
+        y = 0.9 * x
+        xo = torch.empty_like(x)
+        net = ws.CNN(N, g.n, g.n, ws.init_params(0))
+        out["ms"]["cnn_forward"] = timed(lambda: net.forward(x, out=xo), args.reps)
+        out["ms"]["cnn_train_step"] = timed(lambda: net.train_step(x, y, 1e-5), args.reps)
+        net.close()
+        flops = 2.0 * N * g.n * g.n * (6 * 9 * 32 * 32 + 2 * 9 * 32)
+        out["cnn_batch"] = N
+        out["cnn_forward_tflops"] = flops / out["ms"]["cnn_forward"] / 1e9
+        out["cnn_train_tflops"] = 3 * flops / out["ms"]["cnn_train_step"] / 1e9
     print(json.dumps(out))
 
 
