@@ -281,6 +281,9 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
     stream = torch.cuda.current_stream()
 
+    # launch shape of the loop picked by the autotuner on this slice (untimed)
+    tune = plan.tune(p, w, case.beta, 40)
+
     def step():
         # the plain form: FBP start image, then the OS-TV loop
         plan.fbp(p, out=img)
@@ -364,7 +367,10 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, l2="flushed between timed steps (512 MiB write)",
-                       parallelism=f"replicas x{ws}, one slice per GPU per step"),
+                       parallelism=f"replicas x{ws}, one slice per GPU per step",
+                       launch_shape={"view_groups_per_tile": tune["groups"], "grid_blocks": tune["grid_blocks"],
+                                     "autotuned_ms_per_iter": tune["ms_per_iter"],
+                                     "default_ms_per_iter": tune["default_ms_per_iter"]}),
         "gray_per_s": gray, "loop_ms_per_slice": float(np.mean(loop_ms)),
         "setup_and_loop_ms_per_slice": float(np.mean(step_ms)),
         "loop_phase_ms_per_slice": {"reprojection+residual": float(np.mean(fwd_ms)),
@@ -419,6 +425,7 @@ def run_warm(args, dev, ws, plain_slices_per_s):
     IMG = torch.empty((B, g.n, g.n), device=dev)
     betas = [c.beta for c in cases]
     batch.bind(list(P), list(W), betas, list(IMG), K, init_from_input=True, lambda0=lam0)
+    tune = batch.tune(40)                            # view groups per tile (untimed; images restored)
     cnn = wst.CNN(16, g.n, g.n, wst.load_weights())
     s = torch.cuda.Stream()
 
@@ -508,6 +515,9 @@ def run_warm(args, dev, ws, plain_slices_per_s):
         "value": value, "unit": "slices/s", "ms_per_step": t_max / args.steps,
         "speedup_vs_plain": value / plain_slices_per_s if plain_slices_per_s else None,
         "config": dict(WARM_WORKLOAD, seeds=[seeds[0], seeds[-1]],
+                       launch_shape={"view_groups_per_tile": tune["groups"] or "default rule",
+                                     "autotuned_ms_per_iter": tune["ms_per_iter"],
+                                     "default_ms_per_iter": tune["default_ms_per_iter"]},
                        weights="paper_1903_10088_gb300/weights/warmstart_512.npy",
                        l2="flushed between timed steps (512 MiB write)"),
         "stage_ms_per_slice": stage_ms,

@@ -281,6 +281,48 @@ int mvct_cnn_train_step(mvct_cnn cnn, const float *d_in, const float *d_target, 
 int mvct_tv_grad_noalloc(const float *d_img, int32_t n, double eps, float *d_grad,
                          double *d_tv_or_null, void *stream);
 
+/* ---- Autotuner (launch shapes of the loop) ---------------------------------
+ * The loop's work split has two knobs that change speed, not the method: the
+ * blocks of the one-slice launch (co-resident blocks per SM x SMs) and the
+ * number of view groups each 32x32 tile's backprojection (Sec. 4.4
+ * "estimation") is dealt to. The tuners time short runs of every candidate on
+ * the caller's data (each candidate twice, the second run counts) and keep the
+ * fastest; results of a tuned run equal an untuned run up to the summation
+ * order of the groups' partial tiles. */
+#define MVCT_TUNE_MAX 32
+typedef struct mvct_tune_report {
+    int32_t groups;              /* chosen view groups per tile (batch: 0 = the default rule) */
+    int32_t grid_blocks;         /* chosen blocks of the loop launch */
+    double ms_per_iter;          /* loop time per sub-iteration of the choice */
+    double default_ms_per_iter;  /* the same for the untuned default */
+    int32_t n_candidates;        /* entries below (the first is the default) */
+    int32_t cand_groups[MVCT_TUNE_MAX];
+    int32_t cand_grid[MVCT_TUNE_MAX];
+    double cand_ms_per_iter[MVCT_TUNE_MAX];
+} mvct_tune_report;
+
+/* Tune the plan's one-slice loop on (d_sino, d_weights, beta) with n_iter_probe
+ * sub-iterations per run (homogeneous start, default options) and keep the
+ * fastest shape for later mvct_recon calls. Device memory of the caller is only
+ * read; a scratch image is allocated for the duration. report may be NULL.
+ * Synchronises the stream. Errors: as mvct_recon; MVCT_EINVAL for a plan that
+ * belongs to a batch. */
+int mvct_plan_tune(mvct_plan plan, const float *d_sino, const float *d_weights, double beta,
+                   int32_t n_iter_probe, mvct_tune_report *report, void *stream);
+
+/* Set the one-slice launch shape explicitly (e.g. a shape an earlier
+ * mvct_plan_tune reported): groups = view groups per tile (0 = the default
+ * rule, at most min(8, views per subset)), grid_blocks = blocks of the loop
+ * launch (0 = every co-resident block). MVCT_EINVAL outside those ranges. */
+int mvct_plan_set_shape(mvct_plan plan, int32_t groups, int32_t grid_blocks);
+
+/* Tune a bound batch: the view groups per tile of every slice (the default
+ * rule, or 1, 2, 3, 4, 6, 8) with runs of min(n_iter_probe, max_iter)
+ * sub-iterations on the bound data; the bound images are saved before and
+ * restored after the runs, and the batch stays bound with the fastest choice.
+ * Synchronises the stream. report may be NULL. */
+int mvct_batch_tune(mvct_batch batch, int32_t n_iter_probe, mvct_tune_report *report, void *stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *mvct_last_error(void);
 

@@ -156,9 +156,11 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     // `groups` blocks so that tiles x groups fills the grid
     P->tiles_x = (g->n + kTile - 1) / kTile;
     P->n_tiles = P->tiles_x * P->tiles_x;
-    P->groups = std::max(1, std::min(std::min(kMaxGroups, P->geo.Vs), P->recon_grid / P->n_tiles));
-    const size_t part_floats = (size_t)P->n_tiles * P->groups * kTile * kTile;
-    const size_t n_flags = (size_t)P->n_tiles * P->groups;
+    P->groups_cap = std::max(1, std::min(kMaxGroups, P->geo.Vs));
+    P->groups = std::max(1, std::min(P->groups_cap, P->recon_grid / P->n_tiles));
+    P->grid = P->recon_grid;
+    const size_t part_floats = (size_t)P->n_tiles * P->groups_cap * kTile * kTile;
+    const size_t n_flags = (size_t)P->n_tiles * P->groups_cap;
 
     bool ok = cudaMalloc(&P->rays, R * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->views, g->n_views * sizeof(float4)) == cudaSuccess &&

@@ -84,7 +84,11 @@ struct mvct_plan_s {
     float *tile_part = nullptr; // [n_tiles][groups][32*32] partial tiles of the loop's phase B
     float *back_part = nullptr; // [n_tiles][8][32*32] partial tiles of the stand-alone backprojection
     unsigned int *tile_flag = nullptr; // [n_tiles][groups] publication stamps
-    int tiles_x = 0, n_tiles = 0, groups = 1; // phase-B decomposition of the loop kernel
+    int tiles_x = 0, n_tiles = 0;  // phase-B decomposition of the loop kernel: 32x32 tiles,
+    int groups = 1;                // each tile's views dealt to `groups` blocks (one-slice launches)
+    int groups_cap = 1;            // partial-tile buffers allocated for this many groups
+    int tuned_groups = 0;          // > 0: view groups chosen by the autotuner (overrides `groups`)
+    int grid = 0;                  // blocks of one-slice loop launches (<= recon_grid; autotuner)
     double *partials = nullptr; // [partials_cap] per-block FP64 partial sums
     double *partials2 = nullptr;
     int partials_cap = 0;
@@ -147,7 +151,9 @@ inline size_t pad_floats(int n) { return (size_t)(n + 2 * kPadRows) * n; }
 // Largest persistent grid (8 co-resident blocks on each of up to 160 SMs).
 #define MVCT_MAX_RECON_GRID 1280
 int recon_occupancy(mvct_plan_s *P);
-int slice_groups(const mvct_plan_s *P, int nblocks); // view groups per tile for a group of nblocks
+// View groups per tile for a group of nblocks blocks; `override_h` > 0 forces
+// that count (autotuner), clamped to the plan's buffers and its views per subset.
+int slice_groups(const mvct_plan_s *P, int nblocks, int override_h = 0);
 
 } // namespace mvct
 

@@ -413,8 +413,10 @@ int recon_occupancy(mvct_plan_s *P)
     return std::min(nb * P->num_sms, MVCT_MAX_RECON_GRID);
 }
 
-int slice_groups(const mvct_plan_s *P, int nblocks)
+int slice_groups(const mvct_plan_s *P, int nblocks, int override_h)
 {
+    if (override_h > 0) return std::max(1, std::min(override_h, P->groups_cap));
+    if (P->tuned_groups > 0) return std::max(1, std::min(P->tuned_groups, P->groups_cap));
     return std::max(1, std::min(P->groups, nblocks / P->n_tiles));
 }
 
@@ -578,9 +580,9 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     sd.st = (mvct_recon_state *)P->loop_state;
     sd.tiles_x = P->tiles_x;
     sd.n_tiles = P->n_tiles;
-    sd.groups = slice_groups(P, P->recon_grid);
+    sd.groups = slice_groups(P, P->grid);
     sd.beta = (float)beta;
-    GroupDesc gd{0, P->recon_grid, 0, 1, P->d_count, P->partials};
+    GroupDesc gd{0, P->grid, 0, 1, P->d_count, P->partials};
 
     CK(cudaMemcpyAsync(P->loop_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     if (o.lambda_schedule && n_iter > 0)
@@ -588,7 +590,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
     CK(cudaMemsetAsync(P->d_count, 0, 128, st));
     CK(cudaMemsetAsync(P->phase_ns, 0, 2 * sizeof(unsigned long long), st));
-    CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups, st));
+    CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups_cap, st));
 
     Events ev;
     CK(cudaEventRecord(ev.e[0], st));
@@ -638,9 +640,9 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         const void *kern = o.storage == MVCT_STORAGE_BF16  ? (const void *)k_recon<false, __nv_bfloat16>
                            : o.storage == MVCT_STORAGE_F16 ? (const void *)k_recon<false, __half>
                                                            : (const void *)k_recon<false, float>;
-        cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(P->recon_grid), dim3(kThreads), args, 0, st);
+        cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(P->grid), dim3(kThreads), args, 0, st);
         if (le == cudaErrorCooperativeLaunchTooLarge)
-            return mvct_fail(MVCT_ELAUNCH, "mvct_recon: %d blocks cannot be co-resident", P->recon_grid);
+            return mvct_fail(MVCT_ELAUNCH, "mvct_recon: %d blocks cannot be co-resident", P->grid);
         if (le != cudaSuccess)
             return mvct_fail(MVCT_ECUDA, "mvct_recon: cooperative launch: %s", cudaGetErrorString(le));
     }
@@ -676,7 +678,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         stats->loop_ms = t2;
         stats->forward_ms = hphase[0] * 1e-6;
         stats->back_ms = hphase[1] * 1e-6;
-        stats->grid_blocks = P->recon_grid;
+        stats->grid_blocks = P->grid;
         stats->block_threads = kThreads;
     }
     return MVCT_OK;
@@ -687,6 +689,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
 // ---------------------------------------------------------------------------
 struct mvct_batch_s {
     int device = 0, count = 0, grid = 0, ngroups = 0, max_iter = 0;
+    int groups_override = 0;            // > 0: view groups per tile of every slice (autotuner)
     std::vector<mvct_plan_s *> plans;   // user order
     std::vector<int> pos;               // user slice -> position in the descriptor array
     std::vector<int> group_blocks;      // blocks of the group of each user slice
@@ -901,7 +904,7 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
         sd.st = b->d_states + q;
         sd.tiles_x = P->tiles_x;
         sd.n_tiles = P->n_tiles;
-        sd.groups = slice_groups(P, b->group_blocks[i]);
+        sd.groups = slice_groups(P, b->group_blocks[i], b->groups_override);
         sd.beta = (float)betas[i];
     }
     cudaError_t e = cudaMemcpy(b->d_slices, h.data(), sizeof(SliceDesc) * b->count, cudaMemcpyHostToDevice);
@@ -933,7 +936,7 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
     for (int i = 0; i < b->count; ++i) {
         mvct_plan_s *P = b->plans[i];
         const int n = P->geo.n;
-        CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups, st));
+        CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups_cap, st));
         CK(launch_weight_a1(P, b->weights[i], b->sinos[i], P->sino_tmp, &b->d_bar->data_err, st));
         const double cb = b->betas[i] * 8.0 / std::sqrt(o.tv_eps);
         CK(launch_setup_back(P, P->sino_tmp, (float)cb, (float)o.mu0, o.init_from_input ? 1 : 0, b->imgs[i],
@@ -1014,5 +1017,198 @@ extern "C" int mvct_batch_stats(mvct_batch b, int32_t slice, mvct_recon_stats *s
     stats->back_ms = 0.0;
     stats->grid_blocks = b->group_blocks[slice];
     stats->block_threads = kThreads;
+    return MVCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: short loop runs over launch-shape candidates on the caller's data.
+// Candidates change only how the work is split (blocks of the loop launch, view
+// groups per tile), so every candidate computes the same sums up to the order
+// of the per-group partial tiles.
+// ---------------------------------------------------------------------------
+namespace {
+
+void report_add(mvct_tune_report *r, int groups, int grid, double ms)
+{
+    if (!r || r->n_candidates >= MVCT_TUNE_MAX) return;
+    r->cand_groups[r->n_candidates] = groups;
+    r->cand_grid[r->n_candidates] = grid;
+    r->cand_ms_per_iter[r->n_candidates] = ms;
+    r->n_candidates += 1;
+}
+
+} // namespace
+
+extern "C" int mvct_plan_tune(mvct_plan P, const float *d_sino, const float *d_weights, double beta,
+                              int32_t n_iter_probe, mvct_tune_report *report, void *stream)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: null plan");
+    if (!d_sino || !d_weights) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: null device pointer");
+    if (n_iter_probe < 1) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: n_iter_probe must be >= 1");
+    if (P->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: plan belongs to a batch");
+    DeviceGuard dg(P->device);
+    if (report) std::memset(report, 0, sizeof(*report));
+    float *scratch = nullptr;
+    if (cudaMalloc(&scratch, sizeof(float) * (size_t)P->geo.n * P->geo.n) != cudaSuccess) {
+        cudaGetLastError();
+        return mvct_fail(MVCT_ENOMEM, "mvct_plan_tune: scratch image");
+    }
+    const int saved_grid = P->grid, saved_tuned = P->tuned_groups;
+    const int default_groups = slice_groups(P, P->recon_grid, 0);
+    auto probe = [&](int grid, int groups, double *ms) -> int {
+        P->grid = grid;
+        P->tuned_groups = groups;
+        mvct_recon_opts o;
+        mvct_recon_opts_init(&o);
+        mvct_recon_stats st;
+        std::memset(&st, 0, sizeof(st));
+        double best = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) { // the first run warms caches and clocks
+            int rc = mvct_recon(P, d_sino, d_weights, beta, n_iter_probe, &o, scratch, &st, stream);
+            if (rc) return rc;
+            if (rep > 0) best = std::min(best, st.loop_ms / n_iter_probe);
+        }
+        *ms = best;
+        return MVCT_OK;
+    };
+    double default_ms = 0.0;
+    int rc = probe(P->recon_grid, default_groups, &default_ms);
+    int best_grid = P->recon_grid, best_groups = default_groups;
+    double best_ms = default_ms;
+    report_add(report, default_groups, P->recon_grid, default_ms);
+    const int max_bps = P->recon_grid / std::max(1, P->num_sms);
+    const int hs[] = {1, 2, 3, 4, 6, 8};
+    for (int bps = max_bps; rc == MVCT_OK && bps >= std::max(1, max_bps - 2); --bps) {
+        const int grid = std::min(P->recon_grid, bps * P->num_sms);
+        for (int h : hs) {
+            if (h > P->groups_cap || (grid == P->recon_grid && h == default_groups)) continue;
+            double ms = 0.0;
+            rc = probe(grid, h, &ms);
+            if (rc) break;
+            report_add(report, h, grid, ms);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_grid = grid;
+                best_groups = h;
+            }
+        }
+    }
+    cudaFree(scratch);
+    if (rc) {
+        P->grid = saved_grid;
+        P->tuned_groups = saved_tuned;
+        return rc;
+    }
+    P->grid = best_grid;
+    P->tuned_groups = best_groups;
+    if (report) {
+        report->groups = best_groups;
+        report->grid_blocks = best_grid;
+        report->ms_per_iter = best_ms;
+        report->default_ms_per_iter = default_ms;
+    }
+    return MVCT_OK;
+}
+
+extern "C" int mvct_plan_set_shape(mvct_plan P, int32_t groups, int32_t grid_blocks)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "mvct_plan_set_shape: null plan");
+    if (groups < 0 || groups > P->groups_cap)
+        return mvct_fail(MVCT_EINVAL, "mvct_plan_set_shape: groups %d outside 0..%d", groups, P->groups_cap);
+    if (grid_blocks < 0 || grid_blocks > P->recon_grid)
+        return mvct_fail(MVCT_EINVAL, "mvct_plan_set_shape: grid %d outside 0..%d", grid_blocks, P->recon_grid);
+    P->tuned_groups = groups;
+    P->grid = grid_blocks > 0 ? grid_blocks : P->recon_grid;
+    return MVCT_OK;
+}
+
+extern "C" int mvct_batch_tune(mvct_batch b, int32_t n_iter_probe, mvct_tune_report *report, void *stream)
+{
+    if (!b || !b->bound) return mvct_fail(MVCT_EINVAL, "mvct_batch_tune: batch not bound");
+    if (n_iter_probe < 1) return mvct_fail(MVCT_EINVAL, "mvct_batch_tune: n_iter_probe must be >= 1");
+    DeviceGuard dg(b->device);
+    if (report) std::memset(report, 0, sizeof(*report));
+    const int n_it = std::min<int>(n_iter_probe, b->max_iter);
+    if (n_it < 1) return mvct_fail(MVCT_EINVAL, "mvct_batch_tune: the batch was bound with max_iter 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the runs overwrite the bound images: keep copies of the start images
+    std::vector<float *> saved(b->count, nullptr);
+    int rc = MVCT_OK;
+    for (int i = 0; i < b->count && rc == MVCT_OK; ++i) {
+        const size_t bytes = sizeof(float) * (size_t)b->plans[i]->geo.n * b->plans[i]->geo.n;
+        if (cudaMalloc(&saved[i], bytes) != cudaSuccess ||
+            cudaMemcpyAsync(saved[i], b->imgs[i], bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            rc = mvct_fail(MVCT_ENOMEM, "mvct_batch_tune: image copies");
+        }
+    }
+    auto restore = [&]() {
+        for (int i = 0; i < b->count; ++i)
+            if (saved[i])
+                cudaMemcpyAsync(b->imgs[i], saved[i], sizeof(float) * (size_t)b->plans[i]->geo.n * b->plans[i]->geo.n,
+                                cudaMemcpyDeviceToDevice, st);
+    };
+    const int saved_override = b->groups_override;
+    auto probe = [&](int h, double *ms) -> int {
+        b->groups_override = h;
+        // re-bind so the descriptors carry this candidate's view groups
+        std::vector<const float *> s(b->sinos), w(b->weights);
+        std::vector<float *> im(b->imgs);
+        std::vector<double> be(b->betas);
+        const mvct_recon_opts o = b->opts;
+        int r = mvct_batch_bind(b, s.data(), w.data(), be.data(), im.data(), b->max_iter, &o);
+        if (r) return r;
+        double best = INFINITY;
+        for (int rep = 0; rep < 2; ++rep) {
+            restore();
+            r = mvct_batch_run(b, n_it, stream);
+            if (r) return r;
+            mvct_recon_stats stt;
+            std::memset(&stt, 0, sizeof(stt));
+            r = mvct_batch_stats(b, 0, &stt);
+            if (r) return r;
+            if (rep > 0) best = std::min(best, stt.loop_ms / n_it);
+        }
+        *ms = best;
+        return MVCT_OK;
+    };
+    double default_ms = 0.0, best_ms = 0.0;
+    int best_h = 0;
+    if (rc == MVCT_OK) rc = probe(0, &default_ms);
+    best_ms = default_ms;
+    report_add(report, 0, b->grid, default_ms);
+    const int hs[] = {1, 2, 3, 4, 6, 8};
+    for (int h : hs) {
+        if (rc) break;
+        double ms = 0.0;
+        rc = probe(h, &ms);
+        if (rc) break;
+        report_add(report, h, b->grid, ms);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_h = h;
+        }
+    }
+    b->groups_override = rc ? saved_override : best_h;
+    int rc2 = MVCT_OK;
+    {
+        std::vector<const float *> s(b->sinos), w(b->weights);
+        std::vector<float *> im(b->imgs);
+        std::vector<double> be(b->betas);
+        const mvct_recon_opts o = b->opts;
+        rc2 = mvct_batch_bind(b, s.data(), w.data(), be.data(), im.data(), b->max_iter, &o);
+    }
+    restore();
+    cudaStreamSynchronize(st);
+    for (float *p : saved)
+        if (p) cudaFree(p);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    if (report) {
+        report->groups = best_h;
+        report->grid_blocks = b->grid;
+        report->ms_per_iter = best_ms;
+        report->default_ms_per_iter = default_ms;
+    }
     return MVCT_OK;
 }

@@ -92,11 +92,35 @@ class ReconStats(ctypes.Structure):
     ]
 
 
+TUNE_MAX = 32
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [
+        ("groups", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32),
+        ("ms_per_iter", ctypes.c_double),
+        ("default_ms_per_iter", ctypes.c_double),
+        ("n_candidates", ctypes.c_int32),
+        ("cand_groups", ctypes.c_int32 * TUNE_MAX),
+        ("cand_grid", ctypes.c_int32 * TUNE_MAX),
+        ("cand_ms_per_iter", ctypes.c_double * TUNE_MAX),
+    ]
+
+    def to_dict(self) -> dict:
+        k = self.n_candidates
+        return dict(groups=self.groups, grid_blocks=self.grid_blocks, ms_per_iter=self.ms_per_iter,
+                    default_ms_per_iter=self.default_ms_per_iter,
+                    candidates=[dict(groups=self.cand_groups[i], grid_blocks=self.cand_grid[i],
+                                     ms_per_iter=self.cand_ms_per_iter[i]) for i in range(k)])
+
+
 EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
            "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error",
            "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
            "mvct_batch_run", "mvct_batch_stats", "mvct_fbp", "mvct_cnn_param_count", "mvct_cnn_create",
-           "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step"]
+           "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step", "mvct_plan_tune", "mvct_batch_tune",
+           "mvct_plan_set_shape"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -135,6 +159,9 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
                                     ctypes.POINTER(vp), i32, ctypes.POINTER(ReconOpts)]
     lib.mvct_batch_run.argtypes = [vp, i32, vp]
     lib.mvct_batch_stats.argtypes = [vp, i32, ctypes.POINTER(ReconStats)]
+    lib.mvct_plan_tune.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(TuneReport), vp]
+    lib.mvct_batch_tune.argtypes = [vp, i32, ctypes.POINTER(TuneReport), vp]
+    lib.mvct_plan_set_shape.argtypes = [vp, i32, i32]
     lib.mvct_last_error.restype = ctypes.c_char_p
     lib.mvct_last_error.argtypes = []
     return lib
@@ -304,6 +331,25 @@ class Plan:
                                 st.setup_ms, st.grid_blocks, st.forward_ms, st.back_ms)
 
 
+def _plan_tune(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter_probe: int = 40, stream=None) -> dict:
+    """``mvct_plan_tune``: time the loop's launch-shape candidates on (p, w) and
+    keep the fastest for this plan; returns the report as a dict."""
+    R = self.V * self.C
+    rep = TuneReport()
+    _check(lib().mvct_plan_tune(self._h, _dev_f32(p, R, "p"), _dev_f32(w, R, "w"), beta, n_iter_probe,
+                                ctypes.byref(rep), ctypes.c_void_p(_stream(stream))))
+    return rep.to_dict()
+
+
+def _plan_set_shape(self, groups: int = 0, grid_blocks: int = 0) -> None:
+    """``mvct_plan_set_shape``: fix the loop's launch shape (0 = default)."""
+    _check(lib().mvct_plan_set_shape(self._h, groups, grid_blocks))
+
+
+Plan.tune = _plan_tune
+Plan.set_shape = _plan_set_shape
+
+
 def tv_grad_noalloc(img: torch.Tensor, eps: float, grad: torch.Tensor, tv: Optional[torch.Tensor] = None,
                     stream=None) -> None:
     """``mvct_tv_grad_noalloc``: TV gradient (and value) into caller-provided
@@ -373,6 +419,13 @@ class Batch:
     def run(self, n_iter: int, stream=None):
         _check(lib().mvct_batch_run(self._h, n_iter, ctypes.c_void_p(_stream(stream))))
         self.last_n_iter = n_iter
+
+    def tune(self, n_iter_probe: int = 40, stream=None) -> dict:
+        """``mvct_batch_tune``: time the view-group candidates on the bound data
+        (bound images restored afterwards) and keep the fastest."""
+        rep = TuneReport()
+        _check(lib().mvct_batch_tune(self._h, n_iter_probe, ctypes.byref(rep), ctypes.c_void_p(_stream(stream))))
+        return rep.to_dict()
 
     def stats(self, i: int, n_iter: Optional[int] = None) -> ReconResult:
         """Statistics of slice i of the last run (its n_iter sub-iterations)."""
