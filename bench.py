@@ -638,6 +638,47 @@ def run_batched(args):
     return 0
 
 
+def run_subsets(args):
+    """The thinning sweep of the paper's Table I on one 512^2 slice: seconds per
+    slice (FBP start + 500 sub-iterations) and the objective reached, for
+    S in {1, 2, 5, 10, 20, 40}."""
+    import torch
+
+    from paper_1903_10088_gb300 import mvct
+
+    mvct.lib()
+    dev = torch.device("cuda", 0)
+    case = ph.make_case("full", SEED0)
+    g = case.geom
+    p = torch.from_numpy(case.p).to(dev)
+    w = torch.from_numpy(case.w).to(dev)
+    img = torch.empty((g.n, g.n), device=dev)
+    rows = []
+    for S in (1, 2, 5, 10, 20, 40):
+        with mvct.Plan(g, S) as plan:
+            def step():
+                plan.fbp(p, out=img)
+                return plan.recon(p, w, case.beta, case.n_iter, img=img, init_from_input=True)
+            for _ in range(args.warmup):
+                step()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                step()
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            psi = float(plan.objective(img, p, w, case.beta, case.tv_eps).cpu())
+        rows.append({"subsets": S, "s_per_slice": float(np.mean(ms)) / 1e3, "psi_500": psi})
+    print(json.dumps({"metric": "s/slice at 500 sub-iterations vs subsets (paper Table I thinning set)",
+                      "unit": "s/slice", "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+                      "config": dict(WORKLOAD, workload="one 512^2 slice, FBP start, 500 sub-iterations per S"),
+                      "rows": rows, "steps": args.steps, "warmup": args.warmup}))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -648,12 +689,14 @@ def main(argv=None):
                     help="oracle sub-iterations timed per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-started batched form")
-    ap.add_argument("--workload", choices=["plain", "batched"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "batched", "subsets"], default="plain")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "subsets":
+        return run_subsets(args)
     return run_ours(args)
 
 
