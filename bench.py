@@ -352,6 +352,34 @@ def run_ours(args):
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
     gray = 2.0 * taps_per_launch / loop_s / 1e9
 
+    # the stand-alone projector and backprojector (mvct_forward / mvct_back) on the
+    # same slice: tap bytes per call / event time against the same peak
+    def op_time(fn, reps=10):
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps / 1e3
+
+    Vs = g.n_views // case.n_subsets
+    q_all = torch.empty((g.n_views, g.n_channels), device=dev)
+    q_sub = torch.empty((Vs, g.n_channels), device=dev)
+    b_img = torch.empty((g.n, g.n), device=dev)
+    p_sub = p[0::case.n_subsets].contiguous()
+    op_bytes = {"all_views": 4.0 * float(taps.sum()), "one_subset": 4.0 * float(taps[0])}
+    op_s = {"forward_all_views": op_time(lambda: plan.forward(img, -1, out=q_all)),
+            "back_all_views": op_time(lambda: plan.back(p, -1, out=b_img)),
+            "forward_one_subset": op_time(lambda: plan.forward(img, 0, out=q_sub)),
+            "back_one_subset": op_time(lambda: plan.back(p_sub, 0, out=b_img))}
+    operators = {}
+    for k, t in op_s.items():
+        nb = op_bytes["all_views" if "all" in k else "one_subset"]
+        operators[k] = {"ms": t * 1e3, "achieved_gbs": nb / t / 1e9, "frac": nb / t / 1e9 / peaks["hbm_gbs"]}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         t_slice, sample = time_oracle(case, args.ref_sub_iters)
@@ -376,6 +404,9 @@ def run_ours(args):
         "loop_phase_ms_per_slice": {"reprojection+residual": float(np.mean(fwd_ms)),
                                     "estimation+tv+update": float(np.mean(back_ms))},
         "roofline": roofline,
+        "operator_roofline": dict(operators, bytes="4 B x in-image Joseph taps of the call (taps read by the "
+                                                   "projector = residual reads of the matched backprojection)",
+                                  peak_gbs=peaks["hbm_gbs"]),
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "slices/s",
                 "h2d_bytes_per_step": int(hp.numel() * 4 + hw.numel() * 4),

@@ -227,12 +227,28 @@ struct StageSino {
     }
 };
 
+// 32-bit shared-memory addressing for the splat's accumulator read-modify-writes.
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void smem_add(unsigned addr, float v)
+{
+    float old;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(old) : "r"(addr));
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(old + v));
+}
+
 // Splat channels [c0, c1] of one view onto the warp's accumulator tile.
 // pj = j_lo + lane - pc, pi = i_lo + lane - pc.
 template <bool MIRROR, class Stage>
 __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const Stage &load, int c0,
                                                int c1, float pj, float pi, int i_lo, int j_lo, int lane)
 {
+    const unsigned acc0 = smem_addr(acc);
+    // x-driven rays: this lane's column; y-driven rays: this lane's row
+    const unsigned col_x = acc0 + 4u * (unsigned)(MIRROR ? (kTile - 1) - lane : lane);
+    const unsigned row_y = acc0 + 4u * (unsigned)(lane * kAccStride);
     for (int cb = c0; cb <= c1; cb += 32) {
         const int c = cb + lane;
         if (c <= c1) stage[lane] = load(c);
@@ -244,16 +260,22 @@ __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const 
                 float f;
                 const int a = floor_frac(fmaf(r.y, pj, r.x), f) - i_lo;
                 const float w1 = f * r.z, w0 = r.z - w1;
-                const int col = MIRROR ? (kTile - 1) - lane : lane;
-                if ((unsigned)a < (unsigned)kTile) acc[a * kAccStride + col] += w0;
-                if ((unsigned)(a + 1) < (unsigned)kTile) acc[(a + 1) * kAccStride + col] += w1;
+                const unsigned ad = col_x + 4u * (unsigned)(a * kAccStride);
+                if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+                if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u * kAccStride, w1);
             } else {          // y-driven: this lane's row, columns a and a+1
                 float f;
                 const int a = floor_frac(fmaf(r.y, pi, r.x), f) - j_lo;
                 const float w1 = f * r.z, w0 = r.z - w1;
-                float *row = acc + lane * kAccStride;
-                if ((unsigned)a < (unsigned)kTile) row[MIRROR ? (kTile - 1) - a : a] += w0;
-                if ((unsigned)(a + 1) < (unsigned)kTile) row[MIRROR ? (kTile - 2) - a : a + 1] += w1;
+                if (MIRROR) {
+                    const unsigned ad = row_y + 4u * (unsigned)((kTile - 1) - a);
+                    if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+                    if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad - 4u, w1);
+                } else {
+                    const unsigned ad = row_y + 4u * (unsigned)a;
+                    if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+                    if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u, w1);
+                }
             }
         }
         __syncwarp();
