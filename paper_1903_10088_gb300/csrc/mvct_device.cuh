@@ -282,22 +282,25 @@ __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const 
     }
 }
 
-// Each view's channel window is cut into this many parts, dealt to warps.
-constexpr int kParts = 2;
-// Largest number of view groups (blocks) that share one tile in the loop.
+// Largest number of view groups (blocks) that share one tile.
 constexpr int kMaxGroups = 8;
+// Views whose windows are staged in shared memory at a time by splat_views.
+constexpr int kWinBatch = 64;
 
-// One block splats the subset rows k = ka, ka + kstep, ... (< kb) onto the 32x32
-// tile (i_lo, j_lo).
-// Parts of views whose ray slopes are >= 0 go round-robin to warps [0, wpos), the
-// others to warps [wpos, nw) (mirrored layout), wpos = nw/2 (a class without
-// views leaves its warps idle). Returns wpos; after the closing block barrier the
-// tile sum of pixel idx is tile_sum(s_acc, idx, nw, wpos).
+// One block splats subset rows onto the 32x32 tile (i_lo, j_lo): the rows
+// k = order[j] (or k = j without an order) for j = ja, ja + jstep, ... (< jb).
+// Views whose ray slopes are >= 0 go to warps [0, wpos), the others to warps
+// [wpos, nw) (mirrored accumulator layout), wpos = nw/2. Per batch of up to
+// kWinBatch views, the warps first compute the views' channel windows into
+// s_win; then the channels of each class, concatenated in view order, are cut
+// into equal contiguous runs, one per warp of the class (a run may span several
+// views or part of one). Returns wpos; after the closing block barrier the tile
+// sum of pixel idx is tile_sum(s_acc, idx, nw, wpos).
 template <class MakeStage>
 __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restrict__ views, int subset,
-                                           int ka, int kb, int kstep, int i_lo, int j_lo,
-                                           float (*s_acc)[kAccFloats], float4 (*s_stage)[32],
-                                           const MakeStage &make_stage)
+                                           int ja, int jb, int jstep, const int *__restrict__ order,
+                                           int i_lo, int j_lo, float (*s_acc)[kAccFloats],
+                                           float4 (*s_stage)[32], int4 *s_win, const MakeStage &make_stage)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
@@ -310,21 +313,56 @@ __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restric
     const float pj = (float)(j_lo + lane) - g.pc, pi = (float)(i_lo + lane) - g.pc;
     for (int k = lane; k < kAccFloats; k += 32) acc[k] = 0.f;
     __syncwarp();
-    int cnt = 0;
-    for (int k = ka; k < kb; k += kstep) {
-        const int v = subset < 0 ? k : subset + k * g.S;
-        const float4 vw = __ldg(&views[v]);
-        if ((vw.z * vw.w < 0.f) != mirror) continue; // slope class of the view
-        for (int part = 0; part < kParts; ++part, ++cnt) {
-            if (cnt % nmine != q) continue;
+    const int nviews = jb > ja ? (jb - ja + jstep - 1) / jstep : 0;
+    for (int base = 0; base < nviews; base += kWinBatch) {
+        const int cnt = min(kWinBatch, nviews - base);
+        // windows: (c0, c1, mirror class, v) of view `idx` of the batch
+        for (int idx = warp; idx < cnt; idx += nw) {
+            const int j = ja + (base + idx) * jstep;
+            const int k = order ? __ldg(order + j) : j;
+            const int v = subset < 0 ? k : subset + k * g.S;
+            const float4 vw = __ldg(&views[v]);
             const int2 win = tile_window(g, vw, i_lo, j_lo, lane);
-            const int len = win.y - win.x + 1;
-            const int c0 = win.x + (part * len) / kParts, c1 = win.x + ((part + 1) * len) / kParts - 1;
-            if (c1 < c0) continue;
+            if (lane == 0) s_win[idx] = make_int4(win.x, win.y, (vw.z * vw.w < 0.f) ? 1 : 0, k);
+        }
+        __syncthreads();
+        // this class's channel counts of entries lane and lane + 32, exclusive prefix sums
+        int len[2], pre[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int idx = lane + 32 * h;
+            len[h] = 0;
+            if (idx < cnt) {
+                const int4 w = s_win[idx];
+                if ((w.z != 0) == mirror) len[h] = max(0, w.y - w.x + 1);
+            }
+            int x = len[h];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            pre[h] = x - len[h];
+        }
+        const int tot0 = __shfl_sync(0xffffffffu, pre[0] + len[0], 31);
+        pre[1] += tot0;
+        const int total = tot0 + __shfl_sync(0xffffffffu, pre[1] - tot0 + len[1], 31);
+        const int lo = (int)(((long long)q * total) / nmine), hi = (int)(((long long)(q + 1) * total) / nmine);
+        for (int idx = 0; idx < cnt && lo < hi; ++idx) {
+            const int h = idx >> 5, src = idx & 31;
+            const int p0 = __shfl_sync(0xffffffffu, h ? pre[1] : pre[0], src);
+            const int l0 = __shfl_sync(0xffffffffu, h ? len[1] : len[0], src);
+            if (l0 == 0 || p0 + l0 <= lo) continue;
+            if (p0 >= hi) break;
+            const int4 w = s_win[idx];
+            const int c0 = w.x + (max(lo, p0) - p0), c1 = w.x + (min(hi, p0 + l0) - p0) - 1;
+            const int k = w.w;
+            const int v = subset < 0 ? k : subset + k * g.S;
             const auto st = make_stage(k, v);
             if (mirror) splat_channels<true>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
             else splat_channels<false>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
         }
+        __syncthreads(); // s_win is rewritten by the next batch
     }
     __syncthreads();
     return wpos;

@@ -112,11 +112,12 @@ k_back_splat(Geo g, const float4 *__restrict__ rays, const float4 *__restrict__ 
 {
     __shared__ float s_acc[kWarps][kAccFloats];
     __shared__ float4 s_stage[kWarps][32];
+    __shared__ int4 s_win[kWinBatch];
     const int T = tiles_x * tiles_x;
     const int t = blockIdx.x % T, h = blockIdx.x / T;
     const int i_lo = (t / tiles_x) * kTile, j_lo = (t % tiles_x) * kTile;
     const int C = g.C;
-    const int wpos = splat_views(g, views, subset, h, rows, H, i_lo, j_lo, s_acc, s_stage,
+    const int wpos = splat_views(g, views, subset, h, rows, H, nullptr, i_lo, j_lo, s_acc, s_stage, s_win,
                                  [rays, sino, C](int k, int v) {
                                      return StageSino{rays + (size_t)v * C, sino + (size_t)k * C};
                                  });

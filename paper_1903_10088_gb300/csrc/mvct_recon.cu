@@ -62,6 +62,7 @@ struct LoopShared {
     int best_flag, ok;
     float acc[kWarps][kAccFloats]; // warp-private splat tiles
     float4 stage[kWarps][32];      // warp-private ray staging
+    int4 win[kWinBatch];           // channel windows of the splat's views
     SliceDesc sd;                  // batch launches: the current slice
     GroupDesc grp;                 // batch launches: this block's group
 };
@@ -246,7 +247,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             const int t = owner ? item - n_nonowner : item % sd.n_tiles;
             const int h = owner ? H - 1 : item / sd.n_tiles;
             const int i_lo = (t / sd.tiles_x) * kTile, j_lo = (t % sd.tiles_x) * kTile;
-            const int wpos = splat_views(g, sd.views, s, h, g.Vs, H, i_lo, j_lo, sh.acc, sh.stage,
+            const int wpos = splat_views(g, sd.views, s, h, g.Vs, H, nullptr, i_lo, j_lo, sh.acc, sh.stage, sh.win,
                                          [e4, C](int k, int) { return StageE4{e4 + (size_t)k * C}; });
             float part_val[4];
 #pragma unroll
