@@ -23,6 +23,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -118,7 +119,7 @@ class ClockSampler:
     def __init__(self, index: int, tag: str = ""):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{index}{tag}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mvct_clocks_gpu{index}{tag}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -9,8 +9,8 @@
 //                     walked across it with the projector's own weights into
 //                     warp-private shared-memory tiles. No atomics.
 //  * tv_grad_pixel -- gradient of the smoothed isotropic TV (Sec. 2).
-//  * grid_sync     -- grid-wide barrier of the persistent loop with a bounded
-//                     wait (global timer limit plus a spin cap).
+//  * group_sync    -- barrier of a group of blocks of the persistent loop with a
+//                     bounded wait (global timer limit plus a spin cap).
 #pragma once
 
 #include <cuda_bf16.h>
