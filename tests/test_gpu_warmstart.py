@@ -35,7 +35,7 @@ def test_trained_network_gains_over_fbp_start(mvct):
     cases = list(pool.map(ws.case_for, SEEDS))
     dev = torch.device("cuda", torch.cuda.current_device())
     cnn = ws.CNN(8, 512, 512, ws.load_weights())
-    res = ws.evaluate(cnn, cases, KS, dev, width=8, warm_opts={"lambda0": 0.02}, keep_images=2)
+    res = ws.evaluate(cnn, cases, KS, dev, width=8, warm_opts={"lambda0": 0.025}, keep_images=2)
     cnn.close()
     for r in res:
         # the network's image is far closer to the converged one than FBP is
