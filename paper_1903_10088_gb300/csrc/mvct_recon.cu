@@ -54,7 +54,6 @@ __device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int
 
 // Shared state of one block of the loop kernel.
 struct LoopShared {
-    double ring[MVCT_MAX_SUBSETS]; // last S values of Phi of the current slice
     double warp[kWarps];
     double lambda, phi_prev, best_pass;
     long long best_n;
@@ -80,7 +79,6 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
     int *err = &a.gbar->err;
     const Geo &g = sd.g;
     mvct_recon_state *st = sd.st;
-    for (int k = threadIdx.x; k < g.S; k += kThreads) sh.ring[k] = st->phi_ring[k];
     if (threadIdx.x == 0) {
         sh.lambda = st->lambda;
         sh.phi_prev = st->phi_prev;
@@ -190,14 +188,17 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         if (warp == 0) {
             double phi = 0.0;
             for (int k = 0; k < kWarps; ++k) phi += sh.warp[k];
+            // the last S values of Phi live in the slice's state (global memory):
+            // block 0 of the group writes slot n mod S; every block reads the
+            // other slots (written in earlier sub-iterations, ordered by the group
+            // barriers; read past L1) and uses its own Phi_n for slot n mod S
             const int slot_n = (int)(n % g.S);
-            if (lane == 0) sh.ring[slot_n] = phi;
-            __syncwarp();
+            if (lane == 0 && lb == 0) st->phi_ring[slot_n] = phi;
             // pass sum Phi_{n-S+1} + ... + Phi_n: lane-strided, then the warp tree
             double pass = 0.0;
             const bool full = n >= g.S - 1;
             if (full)
-                for (int k = lane; k < g.S; k += 32) pass += sh.ring[k];
+                for (int k = lane; k < g.S; k += 32) pass += (k == slot_n) ? phi : __ldcg(st->phi_ring + k);
             pass = warp_sum(pass);
             if (lane == 0) {
                 double lam;
@@ -336,7 +337,6 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
     }
 
     if (lb == 0) {
-        for (int k = threadIdx.x; k < g.S; k += kThreads) st->phi_ring[k] = sh.ring[k];
         if (threadIdx.x == 0) {
             st->n_done = n0 + a.n_iter;
             st->lambda = sh.lambda;
