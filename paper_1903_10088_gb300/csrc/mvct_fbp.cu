@@ -13,7 +13,10 @@
 namespace mvct {
 
 // One block per view: q[v][c] = a * sum_k R'[k] g[c - k], R' = R * D cos(gamma_k).
-// Only k = c and odd c - k contribute (even offsets of the ramp are zero).
+// Only k = c and odd c - k contribute (even offsets of the ramp are zero). q rows
+// are padded: channel c is stored at c + 2 of a row of C + 4 floats whose two
+// entries at each end are 0, so the backprojection reads channels -2 .. C + 1
+// without bounds tests.
 __global__ void __launch_bounds__(kThreads) k_fbp_filter(Geo g, const float *__restrict__ sino,
                                                         const float *__restrict__ gtab,
                                                         const float *__restrict__ cosw, float a,
@@ -21,14 +24,16 @@ __global__ void __launch_bounds__(kThreads) k_fbp_filter(Geo g, const float *__r
 {
     extern __shared__ float s_pre[]; // [C]
     const int v = blockIdx.x, C = g.C;
+    float *qv = q + (size_t)v * (C + 4);
     for (int c = threadIdx.x; c < C; c += kThreads) s_pre[c] = __ldg(sino + (size_t)v * C + c) * __ldg(cosw + c);
+    if (threadIdx.x < 4) qv[threadIdx.x < 2 ? threadIdx.x : C + threadIdx.x] = 0.f;
     __syncthreads();
     for (int c = threadIdx.x; c < C; c += kThreads) {
         float acc = s_pre[c] * __ldg(gtab + (C - 1));
         // odd offsets d = c - k: k = c - 1, c - 3, ... and k = c + 1, c + 3, ...
         for (int k = c - 1; k >= 0; k -= 2) acc = fmaf(s_pre[k], __ldg(gtab + (C - 1) + (c - k)), acc);
         for (int k = c + 1; k < C; k += 2) acc = fmaf(s_pre[k], __ldg(gtab + (C - 1) + (c - k)), acc);
-        q[(size_t)v * C + c] = a * acc;
+        qv[c + 2] = a * acc;
     }
 }
 
@@ -50,37 +55,52 @@ __device__ __forceinline__ float atan_series(float t)
     return t * s;
 }
 
-// One thread per pixel: f = dbeta * sum_v Q(beta_v, gamma'(x, y)) / L^2, Q linearly
-// interpolated in gamma (0 outside the detector), views in order. The ray angle
-// gamma' = atan(crs / dot) comes from the series above when |crs / dot| <= 0.42
-// (every pixel of a clinical fan, whose half-angle is about 0.24 rad) and from
-// atan2f otherwise.
+// Ray angle gamma' of a pixel seen from the source: atan(crs / dot) from the
+// series when |crs / dot| <= 0.42 (every pixel of a clinical fan, half-angle
+// about 0.24 rad), else atan2f.
+__device__ __forceinline__ float ray_angle(float dot, float crs)
+{
+    const float t = __fdividef(crs, dot);
+    return (dot > 0.f && fabsf(t) <= 0.42f) ? atan_series(t) : atan2f(crs, dot);
+}
+
+// Q(beta_v, gamma') / L^2 of one pixel from the padded filtered row qv (channel c
+// at c + 2): linear interpolation in gamma, channels outside the detector read 0.
+__device__ __forceinline__ float fbp_sample(const Geo &g, const float *__restrict__ qv, float dot, float crs)
+{
+    const float u = fmaf(ray_angle(dot, crs), g.inv_dgamma, g.c_mid);
+    const float fl = floorf(u);
+    const int k = min(max((int)fl, -2), g.C) + 2;
+    const float f = u - fl;
+    const float a0 = __ldg(qv + k), a1 = __ldg(qv + k + 1);
+    return fmaf(f, a1 - a0, a0) * __fdividef(1.f, fmaf(dot, dot, crs * crs));
+}
+
+// Two horizontally adjacent pixels per thread: f = dbeta * sum_v Q(beta_v,
+// gamma'(x, y)) / L^2, views in order. The second pixel's source-relative
+// coordinates are the first's plus delta along x.
 __global__ void __launch_bounds__(kThreads) k_fbp_back(Geo g, const float4 *__restrict__ views,
                                                       const float *__restrict__ q, float dbeta,
                                                       float *__restrict__ img)
 {
-    const int nn = g.n * g.n;
-    for (int r = blockIdx.x * kThreads + threadIdx.x; r < nn; r += gridDim.x * kThreads) {
-        const int i = r / g.n, j = r - i * g.n;
+    const int half = (g.n + 1) >> 1, total = g.n * half;
+    const int Cp = g.C + 4;
+    for (int r = blockIdx.x * kThreads + threadIdx.x; r < total; r += gridDim.x * kThreads) {
+        const int i = r / half, j = 2 * (r - i * half);
         const float x = ((float)j - g.pc) * g.delta, y = ((float)i - g.pc) * g.delta;
-        float acc = 0.f;
+        float acc0 = 0.f, acc1 = 0.f;
         for (int v = 0; v < g.V; ++v) {
             const float4 vw = __ldg(&views[v]);
             const float px = x - vw.x, py = y - vw.y;
             const float dot = fmaf(px, vw.z, py * vw.w);
             const float crs = fmaf(vw.z, py, -vw.w * px);
-            const float t = __fdividef(crs, dot);
-            const float ang = (dot > 0.f && fabsf(t) <= 0.42f) ? atan_series(t) : atan2f(crs, dot);
-            const float u = fmaf(ang, g.inv_dgamma, g.c_mid);
-            const float fl = floorf(u);
-            const int k0 = (int)fl;
-            const float f = u - fl;
-            const float *qv = q + (size_t)v * g.C;
-            const float a0 = ((unsigned)k0 < (unsigned)g.C) ? __ldg(qv + k0) : 0.f;
-            const float a1 = ((unsigned)(k0 + 1) < (unsigned)g.C) ? __ldg(qv + k0 + 1) : 0.f;
-            acc = fmaf(fmaf(f, a1 - a0, a0), __fdividef(1.f, fmaf(dot, dot, crs * crs)), acc);
+            const float *qv = q + (size_t)v * Cp;
+            acc0 += fbp_sample(g, qv, dot, crs);
+            acc1 += fbp_sample(g, qv, fmaf(g.delta, vw.z, dot), fmaf(-g.delta, vw.w, crs));
         }
-        img[r] = dbeta * acc;
+        const size_t o = (size_t)i * g.n + j;
+        img[o] = dbeta * acc0;
+        if (j + 1 < g.n) img[o + 1] = dbeta * acc1;
     }
 }
 
@@ -115,7 +135,8 @@ int mvct_fbp_tables(mvct_plan_s *P)
     for (int c = 0; c < C; ++c)
         cw[c] = (float)(P->g.sad_cm * std::cos((c - (C - 1) / 2.0 + P->g.channel_offset) * a));
     if (cudaMalloc(&P->fbp_g, sizeof(float) * (2 * C - 1)) != cudaSuccess ||
-        cudaMalloc(&P->fbp_cos, sizeof(float) * C) != cudaSuccess)
+        cudaMalloc(&P->fbp_cos, sizeof(float) * C) != cudaSuccess ||
+        cudaMalloc(&P->fbp_q, sizeof(float) * (size_t)P->geo.V * (C + 4)) != cudaSuccess)
         return mvct_fail(MVCT_ENOMEM, "mvct_plan_create: FBP tables");
     if (cudaMemcpy(P->fbp_g, gt.data(), sizeof(float) * (2 * C - 1), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(P->fbp_cos, cw.data(), sizeof(float) * C, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -134,10 +155,10 @@ extern "C" int mvct_fbp(mvct_plan P, const float *d_sino, float *d_img, void *st
     cudaStream_t st = (cudaStream_t)stream;
     const Geo &g = P->geo;
     k_fbp_filter<<<g.V, kThreads, sizeof(float) * g.C, st>>>(g, d_sino, P->fbp_g, P->fbp_cos, P->fbp_a,
-                                                             P->sino_tmp);
-    const int nn = g.n * g.n;
-    const int grid = std::max(1, std::min((nn + kThreads - 1) / kThreads, P->num_sms * 16));
-    k_fbp_back<<<grid, kThreads, 0, st>>>(g, P->views, P->sino_tmp, (float)(2.0 * 3.14159265358979323846 / g.V),
+                                                             P->fbp_q);
+    const int work = g.n * ((g.n + 1) / 2);
+    const int grid = std::max(1, std::min((work + kThreads - 1) / kThreads, P->num_sms * 16));
+    k_fbp_back<<<grid, kThreads, 0, st>>>(g, P->views, P->fbp_q, (float)(2.0 * 3.14159265358979323846 / g.V),
                                           d_img);
     cudaError_t e = cudaGetLastError();
     if (prev != P->device && prev >= 0) cudaSetDevice(prev);

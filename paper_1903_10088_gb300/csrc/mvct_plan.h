@@ -60,6 +60,15 @@ struct LoopArgs {
     int poisson;              // 1: Poisson data term, e = w - exp(-q)
 };
 
+// Batches of up to kParamSlices slices pass their descriptors in the kernel
+// parameters (a __grid_constant__ argument read through the constant cache)
+// instead of global memory copied to shared memory.
+constexpr int kParamSlices = 96;
+struct BatchParams {
+    SliceDesc sl[kParamSlices];
+    GroupDesc gr[kParamSlices];
+};
+
 } // namespace mvct
 
 struct mvct_plan_s {
@@ -107,6 +116,7 @@ struct mvct_plan_s {
     void *p16 = nullptr, *w16 = nullptr;
     float *fbp_g = nullptr;             // [2C-1] fan-beam ramp g(k a)
     float *fbp_cos = nullptr;           // [C] D cos(gamma_c)
+    float *fbp_q = nullptr;             // [V][C+4] filtered rows, channel c at c + 2, zero ends
     float fbp_a = 0.f;                  // channel pitch (rad)
     double *hist = nullptr;     // [2*hist_cap] phi and lambda per sub-iteration
     double *sched = nullptr;    // [hist_cap] lambda schedule

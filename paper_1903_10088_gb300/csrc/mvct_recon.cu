@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <numeric>
 #include <vector>
 
@@ -391,6 +392,28 @@ __global__ void k_to_storage(const float *__restrict__ src, TS *__restrict__ dst
         dst[k] = to_storage<TS>(src[k]);
 }
 
+// The batch loop with its descriptors in the kernel parameters (batches of up
+// to kParamSlices slices): each block's group and slices are read in place.
+template <typename TS = float>
+__global__ void __launch_bounds__(kThreads, 4) k_recon_pb(const __grid_constant__ LoopArgs a,
+                                                          const __grid_constant__ BatchParams bp)
+{
+    __shared__ LoopShared sh;
+    if (*(volatile int *)&a.gbar->data_err) return;
+    unsigned int bk = 0;
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_f = 0, t_b = 0, t_mark = timer ? global_ns() : 0;
+    const GroupDesc &grp = bp.gr[__ldg(a.block_group + blockIdx.x)];
+    const int lb = blockIdx.x - grp.block0;
+    for (int si = 0; si < grp.nslices; ++si)
+        if (!run_slice<TS>(bp.sl[grp.slice0 + si], grp, a, lb, bk, sh, timer && si == 0, t_f, t_b, t_mark)) return;
+    if (timer) {
+        a.phase_ns[0] = t_f;
+        a.phase_ns[1] = t_b;
+    }
+}
+static_assert(sizeof(LoopArgs) + sizeof(BatchParams) <= 32000, "kernel parameters exceed the 32 KB limit");
+
 // Fresh loop state for `count` slices.
 __global__ void k_state_init(mvct_recon_state *st, int count, double lambda0)
 {
@@ -707,6 +730,8 @@ struct mvct_batch_s {
     std::vector<const float *> sinos, weights;
     std::vector<double> betas;
     mvct_recon_opts opts;
+    std::vector<SliceDesc> h_slices;    // descriptor order (for the parameter-space launch)
+    std::vector<GroupDesc> h_groups;
     bool bound = false;
     int last_n_iter = 0;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -829,6 +854,7 @@ extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_bat
         groups[gi].count = b->d_counts + 32 * gi;
         groups[gi].partials = b->d_partials + groups[gi].block0;
     }
+    b->h_groups = groups;
     cudaError_t e = cudaMemcpy(b->d_groups, groups.data(), sizeof(GroupDesc) * b->ngroups, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_block_group, block_group.data(), sizeof(int) * G, cudaMemcpyHostToDevice);
     for (auto &ev : b->ev)
@@ -910,6 +936,7 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
     }
     cudaError_t e = cudaMemcpy(b->d_slices, h.data(), sizeof(SliceDesc) * b->count, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return mvct_fail(MVCT_ECUDA, "mvct_batch_bind: %s", cudaGetErrorString(e));
+    b->h_slices = h;
     b->imgs.assign(d_imgs, d_imgs + b->count);
     b->sinos.assign(d_sinos, d_sinos + b->count);
     b->weights.assign(d_weights, d_weights + b->count);
@@ -963,9 +990,25 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
         a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
         a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
-        void *args[] = {&a};
-        cudaError_t le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads),
-                                                     args, 0, st);
+        cudaError_t le;
+        if (b->count <= kParamSlices && b->ngroups <= kParamSlices) {
+            // descriptors in the kernel parameters (copied at launch, captured by graphs)
+            std::unique_ptr<BatchParams> bp(new BatchParams());
+            std::memcpy(bp->sl, b->h_slices.data(), sizeof(SliceDesc) * b->count);
+            std::memcpy(bp->gr, b->h_groups.data(), sizeof(GroupDesc) * b->ngroups);
+            void *args[] = {&a, bp.get()};
+            le = cudaLaunchCooperativeKernel((const void *)k_recon_pb<float>, dim3(b->grid), dim3(kThreads), args, 0,
+                                             st);
+            if (le != cudaSuccess) { // e.g. fewer co-resident blocks: the descriptor-array kernel
+                cudaGetLastError();
+                void *args1[] = {&a};
+                le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads), args1, 0,
+                                                 st);
+            }
+        } else {
+            void *args[] = {&a};
+            le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads), args, 0, st);
+        }
         if (le == cudaErrorCooperativeLaunchTooLarge)
             return mvct_fail(MVCT_ELAUNCH, "mvct_batch_run: %d blocks cannot be co-resident", b->grid);
         if (le != cudaSuccess)
