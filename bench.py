@@ -426,9 +426,9 @@ def run_ours(args):
 
 
 WARM_WORKLOAD = dict(workload="learned warm start + batched OS-TV: a stack of 48 held-out 512^2 slices per step",
-                     slices=48, n=512, n_views=800, n_channels=738, subsets=20, sub_iterations=80,
+                     slices=48, n=512, n_views=800, n_channels=738, subsets=20, sub_iterations=100,
                      lambda0=0.025, beta=1e-3, tv_eps=1e-6, I0=5e3,
-                     chain="FBP -> CNN (8 conv3x3, 32 ch, BF16 tensor cores) -> 80 OS-TV sub-iterations, "
+                     chain="FBP -> CNN (8 conv3x3, 32 ch, BF16 tensor cores) -> 100 OS-TV sub-iterations, "
                            "all slices in one persistent launch, the whole chain one CUDA-graph replay",
                      quality="objective Psi of every slice against the plain form (FBP start, 500 sub-iterations)")
 
