@@ -94,6 +94,10 @@ typedef struct mvct_recon_opts {
     int32_t debug_unreachable_barrier; /* test knob: the first barrier can never complete */
     int32_t data_term;             /* MVCT_DATA_WLS (0, default) or MVCT_DATA_POISSON (1) */
     int32_t storage;               /* MVCT_STORAGE_F32 (0, default), _BF16 (1) or _F16 (2); mvct_recon only */
+    const int32_t *subset_order;   /* host, S entries: a permutation of 0..S-1 visited cyclically
+                                      (sub-iteration n uses subset subset_order[n mod S]); NULL: the
+                                      paper's equal-interval subsets in order 0, 1, ..., S-1 (Sec. 3.4).
+                                      mvct_recon only; MVCT_EINVAL if not a permutation */
 } mvct_recon_opts;
 
 /* Storage precision of mvct_recon. F32: every buffer FP32. BF16 / F16: the copies

@@ -51,6 +51,7 @@ class OracleParams(ctypes.Structure):
         ("mu0", ctypes.c_double),
         ("init_from_input", ctypes.c_int32),
         ("data_term", ctypes.c_int32),
+        ("subset_order", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -163,12 +164,19 @@ DEFAULTS = dict(lambda0=0.01, dlambda_up=1e-4, dlambda_down=2e-4, lambda_min=1e-
 
 
 def recon(g, n_subsets: int, p, w, beta: float, n_iter: int, init=None, lambda_schedule=None,
-          want_best: bool = False, **params):
-    """Run the OS-TV loop; returns dict(image, phi, lam, best_n, best_pass, best_image)."""
+          want_best: bool = False, subset_order=None, **params):
+    """Run the OS-TV loop; returns dict(image, phi, lam, best_n, best_pass, best_image).
+    subset_order: a permutation of 0..S-1 visited cyclically (default 0, 1, ..., S-1)."""
     prm = dict(DEFAULTS)
     prm.update(params)
+    order = None
+    if subset_order is not None:
+        order = np.ascontiguousarray(subset_order, dtype=np.int32)
+        if sorted(order.tolist()) != list(range(n_subsets)):
+            raise ValueError("subset_order must be a permutation of 0..S-1")
     op = OracleParams(prm["lambda0"], prm["dlambda_up"], prm["dlambda_down"], prm["lambda_min"],
-                      prm["kappa"], prm["tv_eps"], prm["mu0"], 1 if init is not None else 0, prm["data_term"])
+                      prm["kappa"], prm["tv_eps"], prm["mu0"], 1 if init is not None else 0, prm["data_term"],
+                      order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if order is not None else None)
     img = np.zeros((g.n, g.n)) if init is None else _f64(init).reshape(g.n, g.n).copy()
     phi = np.zeros(max(n_iter, 1))
     lam = np.zeros(max(n_iter, 1))

@@ -51,6 +51,7 @@ typedef struct {
     double mu0;             /* homogeneous initial value, 1/cm (Sec. 3.3.2) */
     int32_t init_from_input;/* 1: start from the caller's image instead of mu0 */
     int32_t data_term;      /* 0: weighted least squares on log projections; 1: Poisson log-likelihood */
+    const int32_t *subset_order; /* S entries, a permutation of 0..S-1 visited cyclically; NULL: 0, 1, ..., S-1 */
 } oracle_recon_params;
 
 static const double PI = 3.14159265358979323846;
@@ -298,7 +299,7 @@ int oracle_setup(const oracle_geometry *g, const double *w, double beta, double 
 
 /* The ordered-subset gradient loop (Eq. 3 with Eq. 4-5, Sec. 3.3.2, 3.4, 4.2).
  *
- * Sub-iteration n = 0 .. n_iter-1 uses subset s = n mod S:
+ * Sub-iteration n = 0 .. n_iter-1 uses subset s = n mod S (or subset_order[n mod S]):
  *   q   = A_s mu                         (reprojection of the subset's views)
  *   r   = q - p_s,  Phi_n = sum r^2 (the square difference)
  *   e   = w_s .* r                    (weighted least squares, data_term 0), or
@@ -341,7 +342,7 @@ int oracle_recon(const oracle_geometry *g, int n_subsets, const double *p, const
     double lambda = prm->lambda0, phi_prev = 0.0, best_pass = INFINITY;
     int best_n = -1;
     for (int it = 0; it < n_iter; ++it) {
-        int s = it % S;
+        int s = prm->subset_order ? prm->subset_order[it % S] : it % S;
         oracle_forward(g, img_inout, s, S, q);
         double phi = 0.0;
         for (int k = 0; k < Vs; ++k) {

@@ -31,6 +31,7 @@ struct SliceDesc {
     double *phi_hist;         // [n_iter]
     double *lam_hist;         // [n_iter]
     const double *sched;      // lambda replay schedule (or null)
+    const int *sorder;        // [S] subset visiting order (or null: 0, 1, ..., S-1)
     mvct_recon_state *st;     // loop state (resume in, final out)
     int tiles_x, n_tiles, groups;
     float beta;
@@ -120,6 +121,7 @@ struct mvct_plan_s {
     float fbp_a = 0.f;                  // channel pitch (rad)
     double *hist = nullptr;     // [2*hist_cap] phi and lambda per sub-iteration
     double *sched = nullptr;    // [hist_cap] lambda schedule
+    int *sorder = nullptr;      // [S] subset visiting order of one-slice launches
     int hist_cap = 0;
     int recon_grid = 0;         // co-resident blocks of the loop kernel
     int reduce_grid = 0;        // grid of the grid-stride reduction kernels

@@ -100,7 +100,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
 
     for (int it = 0; it < a.n_iter; ++it) {
         const long long n = n0 + it;
-        const int s = (int)(n % g.S);
+        const int s = sd.sorder ? sd.sorder[(int)(n % g.S)] : (int)(n % g.S);
         const bool odd = (it & 1) != 0;
         const float *cur = odd ? sd.mu1 : sd.mu0;
         const float *curT = odd ? sd.muT1 : sd.muT0;
@@ -519,6 +519,15 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         return mvct_fail(MVCT_EINVAL, "mvct_recon: resuming (state->n_done > 0) needs init_from_input = 1");
     if (o.storage != MVCT_STORAGE_F32 && o.storage != MVCT_STORAGE_BF16 && o.storage != MVCT_STORAGE_F16)
         return mvct_fail(MVCT_EINVAL, "mvct_recon: storage %d unknown", o.storage);
+    if (o.subset_order) {
+        std::vector<char> seen(P->geo.S, 0);
+        for (int k = 0; k < P->geo.S; ++k) {
+            const int v = o.subset_order[k];
+            if (v < 0 || v >= P->geo.S || seen[v])
+                return mvct_fail(MVCT_EINVAL, "mvct_recon: subset_order is not a permutation of 0..%d", P->geo.S - 1);
+            seen[v] = 1;
+        }
+    }
     if (P->recon_grid <= 0) return mvct_fail(MVCT_ELAUNCH, "mvct_recon: loop kernel has no occupancy");
 
     if (P->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_recon: plan belongs to a batch");
@@ -601,6 +610,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     sd.phi_hist = P->hist;
     sd.lam_hist = P->hist + n_iter;
     sd.sched = o.lambda_schedule ? P->sched : nullptr;
+    sd.sorder = o.subset_order ? P->sorder : nullptr;
     sd.st = (mvct_recon_state *)P->loop_state;
     sd.tiles_x = P->tiles_x;
     sd.n_tiles = P->n_tiles;
@@ -611,6 +621,8 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     CK(cudaMemcpyAsync(P->loop_state, &hs, sizeof(hs), cudaMemcpyHostToDevice, st));
     if (o.lambda_schedule && n_iter > 0)
         CK(cudaMemcpyAsync(P->sched, o.lambda_schedule, sizeof(double) * n_iter, cudaMemcpyHostToDevice, st));
+    if (o.subset_order)
+        CK(cudaMemcpyAsync(P->sorder, o.subset_order, sizeof(int) * P->geo.S, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
     CK(cudaMemsetAsync(P->d_count, 0, 128, st));
     CK(cudaMemsetAsync(P->phase_ns, 0, 2 * sizeof(unsigned long long), st));
@@ -886,8 +898,9 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
     mvct_recon_opts o;
     if (opts_in) o = *opts_in;
     else mvct_recon_opts_init(&o);
-    if (o.lambda_schedule || o.state || o.d_best_out)
-        return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: lambda_schedule, state and d_best_out are one-slice options");
+    if (o.lambda_schedule || o.state || o.d_best_out || o.subset_order)
+        return mvct_fail(MVCT_EINVAL,
+                         "mvct_batch_bind: lambda_schedule, state, d_best_out and subset_order are one-slice options");
     if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
         !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
         (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))

@@ -15,7 +15,7 @@ import ctypes
 import math
 import os
 from dataclasses import dataclass
-from typing import Optional
+from typing import List, Optional
 
 import numpy as np
 import torch
@@ -74,6 +74,7 @@ class ReconOpts(ctypes.Structure):
         ("debug_unreachable_barrier", ctypes.c_int32),
         ("data_term", ctypes.c_int32),
         ("storage", ctypes.c_int32),
+        ("subset_order", ctypes.POINTER(ctypes.c_int32)),
     ]
 
 
@@ -204,6 +205,28 @@ def geometry(g) -> Geometry:
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}   # mvct_recon_opts.storage (MVCT_STORAGE_*)
 
 
+def spread_order(S: int) -> List[int]:
+    """A subset visiting order for mvct_recon_opts.subset_order that keeps
+    consecutive subsets far apart in angle: starting at 0, the next subset is the
+    unused one farthest (circularly, in units of the view step) from the last two
+    picks, then from all picks so far, then the smallest index. For S = 20:
+    0, 10, 5, 17, 11, 4, 18, ... (consecutive subsets 6-10 view steps apart). The
+    paper's order is 0, 1, ..., S-1."""
+    order, used = [0], {0}
+    cd = lambda a, b: min(abs(a - b), S - abs(a - b))
+    while len(order) < S:
+        key, best = None, None
+        for s in range(S):
+            if s in used:
+                continue
+            k = (min(cd(s, u) for u in order[-2:]), min(cd(s, u) for u in used), -s)
+            if key is None or k > key:
+                key, best = k, s
+        order.append(best)
+        used.add(best)
+    return order
+
+
 @dataclass
 class ReconResult:
     phi: np.ndarray
@@ -304,6 +327,10 @@ class Plan:
         lib().mvct_recon_opts_init(ctypes.byref(o))
         if isinstance(opts.get("storage"), str):
             opts = dict(opts, storage=STORAGE[opts["storage"]])
+        order = None
+        if opts.get("subset_order") is not None:
+            order = np.ascontiguousarray(opts["subset_order"], dtype=np.int32)
+            opts = dict(opts, subset_order=order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")

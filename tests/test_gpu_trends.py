@@ -81,3 +81,16 @@ def test_forty_subsets_need_more_than_500(mvct, case, capsys):
         print(f"\nPsi: S=20 @500 {psi20:.4f}; S=40 @500 {psi40[500]:.4f}, @1000 {psi40[1000]:.4f}")
     assert psi40[500] > psi20
     assert psi40[1000] < psi40[500]
+
+
+def test_spread_subset_order(mvct, case, capsys):
+    """The paper visits its equal-interval subsets in an unstated order (read as
+    0, 1, ..., S-1); a spread order (consecutive subsets far apart in angle) is
+    measured beside it."""
+    order = mvct.spread_order(20)
+    seq = psi_curve(mvct, case, 20, [50, 100, 200, 500])
+    spr = psi_curve(mvct, case, 20, [50, 100, 200, 500], subset_order=order)
+    with capsys.disabled():
+        print("\nPsi sequential:", {k: round(v, 4) for k, v in seq.items()},
+              "\nPsi spread:    ", {k: round(v, 4) for k, v in spr.items()})
+    assert all(np.isfinite(v) for v in spr.values())
