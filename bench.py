@@ -449,37 +449,17 @@ def run_warm(args, dev, ws, plain_slices_per_s):
     seeds = range(wst.HELDOUT_SEED0 + rank * B, wst.HELDOUT_SEED0 + (rank + 1) * B)
     cases = wst.make_cases(seeds, workers=min(16, os.cpu_count() or 1))
     g = cases[0].geom
-    plans = [mvct.Plan(g, cases[0].n_subsets) for _ in range(B)]
-    batch = mvct.Batch(plans)
-    P = torch.stack([torch.from_numpy(c.p) for c in cases]).to(dev)
-    W = torch.stack([torch.from_numpy(c.w) for c in cases]).to(dev)
-    X = torch.empty((B, g.n, g.n), device=dev)
-    IMG = torch.empty((B, g.n, g.n), device=dev)
+    pipe = wst.WarmPipeline(g, cases[0].n_subsets, B, K, dev, lambda0=lam0)
     betas = [c.beta for c in cases]
-    batch.bind(list(P), list(W), betas, list(IMG), K, init_from_input=True, lambda0=lam0)
-    tune = batch.tune(40)                            # view groups per tile (untimed; images restored)
-    cnn = wst.CNN(16, g.n, g.n, wst.load_weights())
-    s = torch.cuda.Stream()
-
-    def chain(st):
-        for k in range(B):
-            plans[k].fbp(P[k], out=X[k], stream=st)
-        wst.infer(cnn, X, out=IMG, stream=st)
-        batch.run(K, stream=st)
-
-    s.wait_stream(torch.cuda.current_stream())
-    chain(s)                                         # once outside capture
-    torch.cuda.synchronize()
-    batch.stats(0)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        with torch.cuda.graph(graph, stream=s):
-            chain(s)
-    torch.cuda.synchronize()
+    pipe.load(torch.stack([torch.from_numpy(c.p) for c in cases]), torch.stack([torch.from_numpy(c.w) for c in cases]),
+              betas)
+    P, W, IMG, plans, batch = pipe.p, pipe.w, pipe.img, pipe.plans, pipe.batch
+    tune = pipe.tune(40)                             # view groups per tile (untimed; images restored)
+    pipe.capture()
     for _ in range(args.warmup):
-        graph.replay()
+        pipe.run()
     torch.cuda.synchronize()
-    batch.stats(0)                                   # raises if a run failed
+    pipe.check()                                     # raises if a run failed
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
     cur = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -489,7 +469,7 @@ def run_warm(args, dev, ws, plain_slices_per_s):
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(cur)
-            graph.replay()
+            pipe.run()
             ev[k][1].record(cur)
         torch.cuda.synchronize()
     barrier()
@@ -497,19 +477,8 @@ def run_warm(args, dev, ws, plain_slices_per_s):
     t_max = max_over_ranks(float(np.sum(step_ms)), dev)
     value = B * ws * args.steps / (t_max / 1e3)
 
-    # stage times of one untimed chain (events between the stages)
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    e[0].record(cur)
-    for k in range(B):
-        plans[k].fbp(P[k], out=X[k])
-    e[1].record(cur)
-    wst.infer(cnn, X, out=IMG)
-    e[2].record(cur)
-    batch.run(K)
-    e[3].record(cur)
-    torch.cuda.synchronize()
-    stage_ms = {"fbp": e[0].elapsed_time(e[1]) / B, "cnn": e[1].elapsed_time(e[2]) / B,
-                "setup_and_loop": e[2].elapsed_time(e[3]) / B}
+    # stage times of one untimed direct chain (events between the stages)
+    stage_ms = pipe.stage_ms()
 
     # end to end: host sinograms and weights in, host images out
     hP, hW = P.cpu().pin_memory(), W.cpu().pin_memory()
@@ -521,7 +490,7 @@ def run_warm(args, dev, ws, plain_slices_per_s):
         e0.record(cur)
         P.copy_(hP, non_blocking=True)
         W.copy_(hW, non_blocking=True)
-        graph.replay()
+        pipe.run()
         hI.copy_(IMG, non_blocking=True)
         e1.record(cur)
         torch.cuda.synchronize()
@@ -531,7 +500,7 @@ def run_warm(args, dev, ws, plain_slices_per_s):
     # quality: Psi of the warm-started results against the plain form
     psi = lambda k, im: float(plans[0].objective(im, P[k], W[k], cases[k].beta, cases[k].tv_eps).item())
     psi_warm = np.array([psi(k, IMG[k]) for k in range(B)])
-    graph = None
+    pipe.graph = None
     for k in range(B):
         plans[k].fbp(P[k], out=IMG[k])
     batch.bind(list(P), list(W), betas, list(IMG), 500, init_from_input=True)
@@ -539,10 +508,7 @@ def run_warm(args, dev, ws, plain_slices_per_s):
     batch.stats(0)
     psi_plain = np.array([psi(k, IMG[k]) for k in range(B)])
     gap = (psi_warm - psi_plain) / psi_plain
-    cnn.close()
-    batch.close()
-    for pl in plans:
-        pl.close()
+    pipe.close()
     return {
         "value": value, "unit": "slices/s", "ms_per_step": t_max / args.steps,
         "speedup_vs_plain": value / plain_slices_per_s if plain_slices_per_s else None,

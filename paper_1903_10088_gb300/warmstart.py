@@ -352,6 +352,112 @@ def summarize(results, Ks, tol: float = 1e-3):
     return s
 
 
+class WarmPipeline:
+    """The warm-started, batched reconstruction of a stack of same-geometry slices:
+    FBP of every slice (``mvct_fbp``), the network's start images
+    (``mvct_cnn_forward``), and K OS-TV sub-iterations of all slices in one
+    persistent launch (``mvct_batch_run``), optionally captured as one CUDA graph.
+
+        pipe = WarmPipeline(geom, n_subsets, slices, K, device)
+        pipe.load(p, w, betas)          # [B][V][C] tensors (host or device)
+        pipe.tune()                     # optional: the batch autotuner
+        pipe.capture()                  # optional: one CUDA graph for the chain
+        pipe.run()                      # enqueue the chain; images in pipe.img
+    """
+
+    def __init__(self, geom, n_subsets: int, slices: int, K: int, device, lambda0: float = 0.025,
+                 weights: Optional[np.ndarray] = None, cnn_batch: int = 16):
+        torch = _torch()
+        from . import mvct
+
+        self.geom, self.S, self.B, self.K, self.device = geom, n_subsets, slices, K, device
+        self.lambda0 = lambda0
+        self.plans = [mvct.Plan(geom, n_subsets) for _ in range(slices)]
+        self.batch = mvct.Batch(self.plans)
+        self.p = torch.zeros((slices, geom.n_views, geom.n_channels), device=device)
+        self.w = torch.zeros_like(self.p)
+        self.fbp = torch.zeros((slices, geom.n, geom.n), device=device)
+        self.img = torch.zeros_like(self.fbp)
+        self.cnn = CNN(min(cnn_batch, slices), geom.n, geom.n, load_weights() if weights is None else weights)
+        self.stream = torch.cuda.Stream(device=device)
+        self.graph = None
+        self.betas = None
+
+    def load(self, p, w, betas):
+        """Copy the stack's log projections and weights ([B][V][C]) and bind the batch."""
+        self.p.copy_(p, non_blocking=True)
+        self.w.copy_(w, non_blocking=True)
+        betas = [float(b) for b in betas]
+        if betas != self.betas:
+            self.batch.bind(list(self.p), list(self.w), betas, list(self.img), self.K, init_from_input=True,
+                            lambda0=self.lambda0)
+            self.betas = betas
+            self.graph = None
+
+    def tune(self, n_iter_probe: int = 40) -> dict:
+        """The batch autotuner on the loaded stack (view groups per tile)."""
+        self.graph = None
+        return self.batch.tune(n_iter_probe)
+
+    def _chain(self, st, marks=None):
+        torch = _torch()
+        if marks:
+            marks[0].record(st)
+        for k in range(self.B):
+            self.plans[k].fbp(self.p[k], out=self.fbp[k], stream=st)
+        if marks:
+            marks[1].record(st)
+        infer(self.cnn, self.fbp, out=self.img, stream=st)
+        if marks:
+            marks[2].record(st)
+        self.batch.run(self.K, stream=st)
+        if marks:
+            marks[3].record(st)
+
+    def capture(self):
+        """Run the chain once, then capture it as one CUDA graph."""
+        torch = _torch()
+        st = self.stream
+        st.wait_stream(torch.cuda.current_stream(self.device))
+        self._chain(st)
+        torch.cuda.synchronize(self.device)
+        self.batch.stats(0)                       # raises if the run failed
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                self._chain(st)
+        torch.cuda.synchronize(self.device)
+        self.graph = g
+
+    def run(self):
+        """Enqueue the chain on the current stream (the captured graph if any)."""
+        torch = _torch()
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._chain(torch.cuda.current_stream(self.device))
+
+    def stage_ms(self) -> dict:
+        """Device time per slice of the three stages of one direct (uncaptured) run."""
+        torch = _torch()
+        marks = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        self._chain(torch.cuda.current_stream(self.device), marks)
+        torch.cuda.synchronize(self.device)
+        return {"fbp": marks[0].elapsed_time(marks[1]) / self.B, "cnn": marks[1].elapsed_time(marks[2]) / self.B,
+                "setup_and_loop": marks[2].elapsed_time(marks[3]) / self.B}
+
+    def check(self):
+        """Raise if the last run failed (data check or barrier timeout)."""
+        self.batch.stats(0)
+
+    def close(self):
+        self.graph = None
+        self.cnn.close()
+        self.batch.close()
+        for p in self.plans:
+            p.close()
+
+
 def weights_path() -> str:
     import os
 

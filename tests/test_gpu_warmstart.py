@@ -72,3 +72,40 @@ def test_training_from_scratch_gains(mvct):
     for r in res:
         assert r["psi_cnn_K10"] < r["psi_fbp_K10"], r["seed"]
         assert r["rel_plain_cnn_K0"] < r["rel_plain_fbp_K0"]
+
+
+def test_warm_pipeline_graph_equals_direct_run(mvct):
+    """WarmPipeline (FBP -> network -> batched loop): the CUDA-graph replay gives
+    the same images as the direct chain, bit for bit, and they match running the
+    three stages by hand."""
+    cases = [ws.case_for(s) for s in range(ws.HELDOUT_SEED0 + 110, ws.HELDOUT_SEED0 + 113)]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pipe = ws.WarmPipeline(cases[0].geom, cases[0].n_subsets, len(cases), 20, dev)
+    pipe.load(torch.stack([torch.from_numpy(c.p) for c in cases]),
+              torch.stack([torch.from_numpy(c.w) for c in cases]), [c.beta for c in cases])
+    pipe.run()
+    torch.cuda.synchronize()
+    pipe.check()
+    direct = pipe.img.clone()
+    fbp = pipe.fbp.clone()
+    pipe.capture()
+    pipe.img.zero_()
+    pipe.run()
+    torch.cuda.synchronize()
+    pipe.check()
+    assert torch.equal(direct, pipe.img)
+    assert torch.isfinite(direct).all()
+    # by hand: the network's start, then the batch from it
+    start = ws.infer(pipe.cnn, fbp)
+    pipe.close()
+    plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
+    imgs = [start[k].clone() for k in range(len(cases))]
+    with mvct.Batch(plans) as b:
+        b.bind([torch.from_numpy(c.p).to(dev) for c in cases], [torch.from_numpy(c.w).to(dev) for c in cases],
+               [c.beta for c in cases], imgs, 20, init_from_input=True, lambda0=0.025)
+        b.run(20)
+        b.stats(0)
+    for k in range(len(cases)):
+        assert torch.equal(imgs[k], direct[k])
+    for pl in plans:
+        pl.close()
