@@ -23,6 +23,28 @@ int mvct_fail(int code, const char *fmt, ...)
 
 extern "C" const char *mvct_last_error(void) { return g_err; }
 
+int mvct_check_ptrs(int device, void *stream, const char *who, std::initializer_list<const void *> ptrs)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        cs = cudaStreamCaptureStatusNone;
+    }
+    for (const void *p : ptrs) {
+        if (!p) return mvct_fail(MVCT_EINVAL, "%s: null device pointer", who);
+        if (cs != cudaStreamCaptureStatusNone) continue;
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+            cudaGetLastError();
+            return mvct_fail(MVCT_EINVAL, "%s: %p is not CUDA memory", who, p);
+        }
+        if (a.type == cudaMemoryTypeManaged) continue;
+        if (a.type != cudaMemoryTypeDevice || a.device != device)
+            return mvct_fail(MVCT_EINVAL, "%s: %p is not device memory of device %d", who, p, device);
+    }
+    return MVCT_OK;
+}
+
 namespace {
 
 struct DeviceGuard {
@@ -234,7 +256,8 @@ extern "C" int mvct_forward(mvct_plan P, const float *d_img, float *d_sino, int3
 {
     int rc = check_plan_subset(P, subset, "mvct_forward");
     if (rc) return rc;
-    if (!d_img || !d_sino) return mvct_fail(MVCT_EINVAL, "mvct_forward: null device pointer");
+    rc = mvct_check_ptrs(P->device, stream, "mvct_forward", {d_img, d_sino});
+    if (rc) return rc;
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
     float *img = pad_row0(P->pad[0], P->geo.n), *imgT = pad_row0(P->pad[2], P->geo.n);
@@ -247,7 +270,8 @@ extern "C" int mvct_back(mvct_plan P, const float *d_sino, float *d_img, int32_t
 {
     int rc = check_plan_subset(P, subset, "mvct_back");
     if (rc) return rc;
-    if (!d_img || !d_sino) return mvct_fail(MVCT_EINVAL, "mvct_back: null device pointer");
+    rc = mvct_check_ptrs(P->device, stream, "mvct_back", {d_img, d_sino});
+    if (rc) return rc;
     DeviceGuard dg(P->device);
     CK(launch_back(P, d_sino, d_img, subset, (cudaStream_t)stream));
     return MVCT_OK;
@@ -257,7 +281,9 @@ extern "C" int mvct_tv_grad(mvct_plan P, const float *d_img, double eps, float *
                             double *d_tv_or_null, void *stream)
 {
     if (!P) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: null plan");
-    if (!d_img || !d_grad) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: null device pointer");
+    int rc = mvct_check_ptrs(P->device, stream, "mvct_tv_grad", {d_img, d_grad});
+    if (rc == MVCT_OK && d_tv_or_null) rc = mvct_check_ptrs(P->device, stream, "mvct_tv_grad", {d_tv_or_null});
+    if (rc) return rc;
     if (!(eps > 0) || !std::isfinite(eps)) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: eps must be > 0");
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -271,8 +297,8 @@ extern "C" int mvct_objective(mvct_plan P, const float *d_img, const float *d_si
                               double beta, double eps, double *d_out, void *stream)
 {
     if (!P) return mvct_fail(MVCT_EINVAL, "mvct_objective: null plan");
-    if (!d_img || !d_sino || !d_weights || !d_out)
-        return mvct_fail(MVCT_EINVAL, "mvct_objective: null device pointer");
+    int rc = mvct_check_ptrs(P->device, stream, "mvct_objective", {d_img, d_sino, d_weights, d_out});
+    if (rc) return rc;
     if (!(eps > 0) || !std::isfinite(eps) || !std::isfinite(beta))
         return mvct_fail(MVCT_EINVAL, "mvct_objective: invalid beta/eps");
     DeviceGuard dg(P->device);

@@ -734,7 +734,8 @@ extern "C" int mvct_cnn_forward(mvct_cnn c, const float *d_in, int32_t n, float 
 {
     int rc = check_batch(c, n);
     if (rc) return rc;
-    if (!d_in || !d_out) return mvct_fail(MVCT_EINVAL, "mvct_cnn_forward: null device pointer");
+    rc = mvct_check_ptrs(c->device, stream, "mvct_cnn_forward", {d_in, d_out});
+    if (rc) return rc;
     Dev d(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     const long long pix = (long long)n * c->H * c->W;
@@ -771,7 +772,9 @@ extern "C" int mvct_cnn_grad(mvct_cnn c, const float *d_in, const float *d_targe
 {
     int rc = check_batch(c, n);
     if (rc) return rc;
-    if (!d_in || !d_target) return mvct_fail(MVCT_EINVAL, "mvct_cnn_grad: null device pointer");
+    rc = mvct_check_ptrs(c->device, stream, "mvct_cnn_grad", {d_in, d_target});
+    if (rc == MVCT_OK && d_grad) rc = mvct_check_ptrs(c->device, stream, "mvct_cnn_grad", {d_grad});
+    if (rc) return rc;
     Dev d(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     rc = loss_and_grad(c, d_in, d_target, n, loss, st);
@@ -785,7 +788,9 @@ extern "C" int mvct_cnn_train_step(mvct_cnn c, const float *d_in, const float *d
 {
     int rc = check_batch(c, n);
     if (rc) return rc;
-    if (!d_in || !d_target || !(lr > 0)) return mvct_fail(MVCT_EINVAL, "mvct_cnn_train_step: invalid arguments");
+    if (!(lr > 0)) return mvct_fail(MVCT_EINVAL, "mvct_cnn_train_step: lr must be > 0");
+    rc = mvct_check_ptrs(c->device, stream, "mvct_cnn_train_step", {d_in, d_target});
+    if (rc) return rc;
     Dev d(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     rc = loss_and_grad(c, d_in, d_target, n, loss, st);

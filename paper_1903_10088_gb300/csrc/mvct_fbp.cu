@@ -148,7 +148,10 @@ int mvct_fbp_tables(mvct_plan_s *P)
 extern "C" int mvct_fbp(mvct_plan P, const float *d_sino, float *d_img, void *stream)
 {
     if (!P) return mvct_fail(MVCT_EINVAL, "mvct_fbp: null plan");
-    if (!d_sino || !d_img) return mvct_fail(MVCT_EINVAL, "mvct_fbp: null device pointer");
+    {
+        const int rc = mvct_check_ptrs(P->device, stream, "mvct_fbp", {d_sino, d_img});
+        if (rc) return rc;
+    }
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != P->device) cudaSetDevice(P->device);

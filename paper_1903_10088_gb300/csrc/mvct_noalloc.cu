@@ -64,6 +64,11 @@ extern "C" int mvct_tv_grad_noalloc(const float *d_img, int32_t n, double eps, f
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return mvct_fail(MVCT_ECUDA, "mvct_tv_grad_noalloc: %s", cudaGetErrorString(e));
+    {
+        int rc = mvct_check_ptrs(dev, stream, "mvct_tv_grad_noalloc", {d_img, d_grad});
+        if (rc == MVCT_OK && d_tv_or_null) rc = mvct_check_ptrs(dev, stream, "mvct_tv_grad_noalloc", {d_tv_or_null});
+        if (rc) return rc;
+    }
     if (dev < 0 || dev >= kMaxDevices)
         return mvct_fail(MVCT_EINVAL, "mvct_tv_grad_noalloc: device ordinal %d >= %d", dev, kMaxDevices);
     DeviceScratch s;

@@ -174,3 +174,8 @@ int mvct_fbp_tables(mvct_plan_s *P);
 
 // Error reporting shared by the translation units (mvct_api.cu).
 int mvct_fail(int code, const char *fmt, ...);
+
+// Every pointer must be non-null device (or managed) memory of `device`:
+// otherwise MVCT_EINVAL naming `who`, before anything is launched. While
+// `stream` is being captured into a CUDA graph only the null test is made.
+int mvct_check_ptrs(int device, void *stream, const char *who, std::initializer_list<const void *> ptrs);

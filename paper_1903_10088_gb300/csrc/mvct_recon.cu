@@ -504,8 +504,14 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
                           mvct_recon_stats *stats, void *stream)
 {
     if (!P) return mvct_fail(MVCT_EINVAL, "mvct_recon: null plan");
-    if (!d_sino || !d_weights || !d_img_inout)
-        return mvct_fail(MVCT_EINVAL, "mvct_recon: null device pointer");
+    {
+        const int rc = mvct_check_ptrs(P->device, stream, "mvct_recon", {d_sino, d_weights, d_img_inout});
+        if (rc) return rc;
+        if (opts_in && opts_in->d_best_out) {
+            const int rc2 = mvct_check_ptrs(P->device, stream, "mvct_recon", {opts_in->d_best_out});
+            if (rc2) return rc2;
+        }
+    }
     if (n_iter < 0) return mvct_fail(MVCT_EINVAL, "mvct_recon: n_iter < 0");
     if (!std::isfinite(beta) || beta < 0) return mvct_fail(MVCT_EINVAL, "mvct_recon: beta must be finite and >= 0");
     mvct_recon_opts o;
@@ -909,6 +915,8 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
     for (int i = 0; i < b->count; ++i) {
         if (!d_sinos[i] || !d_weights[i] || !d_imgs[i])
             return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: null device pointer for slice %d", i);
+        const int rc = mvct_check_ptrs(b->device, nullptr, "mvct_batch_bind", {d_sinos[i], d_weights[i], d_imgs[i]});
+        if (rc) return rc;
         if (!std::isfinite(betas[i]) || betas[i] < 0)
             return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: beta of slice %d must be finite and >= 0", i);
     }
@@ -1100,7 +1108,10 @@ extern "C" int mvct_plan_tune(mvct_plan P, const float *d_sino, const float *d_w
                               int32_t n_iter_probe, mvct_tune_report *report, void *stream)
 {
     if (!P) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: null plan");
-    if (!d_sino || !d_weights) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: null device pointer");
+    {
+        const int rc = mvct_check_ptrs(P->device, stream, "mvct_plan_tune", {d_sino, d_weights});
+        if (rc) return rc;
+    }
     if (n_iter_probe < 1) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: n_iter_probe must be >= 1");
     if (P->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_plan_tune: plan belongs to a batch");
     DeviceGuard dg(P->device);

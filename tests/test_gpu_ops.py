@@ -200,3 +200,22 @@ def test_fbp_full_size_sampled(mvct):
         img = host(plan.fbp(cuda(c.p)))
     ref = F.fbp(c.geom, c.p.astype(np.float64))
     assert rel(img, ref) < 1e-4
+
+
+def test_host_pointer_rejected_before_launch(mvct):
+    """The C ABI checks that every pointer is device memory of the plan's device
+    before it launches anything: a host buffer gives MVCT_EINVAL."""
+    import ctypes
+
+    g = ph.GEOM_128
+    host = torch.zeros((g.n, g.n), dtype=torch.float32).pin_memory()
+    dev = torch.zeros((g.n_views, g.n_channels), device="cuda")
+    with mvct.Plan(g, 1) as plan:
+        rc = mvct.lib().mvct_forward(plan._h, ctypes.c_void_p(host.data_ptr()), ctypes.c_void_p(dev.data_ptr()),
+                                     -1, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == -1
+        assert b"not device memory" in mvct.lib().mvct_last_error()
+        rc = mvct.lib().mvct_fbp(plan._h, ctypes.c_void_p(dev.data_ptr()), ctypes.c_void_p(host.data_ptr()),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        assert rc == -1
+    torch.cuda.synchronize()
