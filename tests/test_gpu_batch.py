@@ -128,3 +128,54 @@ def test_batch_argument_errors(mvct):
     with pytest.raises(mvct.MvctError):
         mvct.Batch([plan, plan])           # a plan twice
     plan.close()
+
+
+def test_batch_barrier_timeout_reports_and_recovers(mvct):
+    """A group barrier that can never complete (host-side test knob, 50 ms limit)
+    ends the batch run with MVCT_ETIMEOUT read by the host; the context stays
+    usable and the next bound run matches the reference."""
+    cases = make_cases(4, seed0=430)
+    plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
+    p = [cuda(c.p) for c in cases]
+    w = [cuda(c.w) for c in cases]
+    imgs = [torch.zeros((c.geom.n, c.geom.n), device="cuda") for c in cases]
+    with mvct.Batch(plans) as b:
+        b.bind(p, w, [c.beta for c in cases], imgs, 4, debug_unreachable_barrier=1, barrier_timeout_ms=50.0)
+        b.run(4)
+        with pytest.raises(mvct.MvctError) as ei:
+            b.stats(0)
+        assert ei.value.code == -5          # MVCT_ETIMEOUT
+        b.bind(p, w, [c.beta for c in cases], imgs, 4)
+        b.run(4)
+        b.stats(0)
+        ok = [im.clone() for im in imgs]
+    for i, c in enumerate(cases):
+        ref = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, 4)
+        assert rel(ok[i].cpu().numpy(), ref["image"]) < RTOL_IMG
+    for pl in plans:
+        pl.close()
+
+
+def test_large_batch_descriptor_array_path(mvct):
+    """Batches of more than 96 slices keep their descriptors in global memory
+    (the other kernel variant): 100 small slices of two geometries against the
+    one-slice runs of the same data."""
+    geoms = [ph.Geometry(n=24, n_views=40, n_channels=36), ph.Geometry(n=16, n_views=30, n_channels=28)]
+    cases = [ph.make_case("small", 600 + k, geom=geoms[k % 2], n_subsets=5 if k % 2 == 0 else 3, n_iter=6)
+             for k in range(100)]
+    plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
+    p = [cuda(c.p) for c in cases]
+    w = [cuda(c.w) for c in cases]
+    imgs = [torch.zeros((c.geom.n, c.geom.n), device="cuda") for c in cases]
+    with mvct.Batch(plans) as b:
+        b.bind(p, w, [c.beta for c in cases], imgs, 6)
+        b.run(6)
+        b.stats(0)
+        got = [im.clone() for im in imgs]
+    for pl in plans:
+        pl.close()
+    for k in (0, 1, 57, 98, 99):
+        c = cases[k]
+        with mvct.Plan(c.geom, c.n_subsets) as plan:
+            single, _ = plan.recon(cuda(c.p), cuda(c.w), c.beta, 6)
+        assert rel(got[k].cpu().numpy(), single.cpu().numpy()) < 1e-5
