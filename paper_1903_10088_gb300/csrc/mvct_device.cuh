@@ -240,7 +240,9 @@ __device__ __forceinline__ void smem_add(unsigned addr, float v)
 }
 
 // Splat channels [c0, c1] of one view onto the warp's accumulator tile.
-// pj = j_lo + lane - pc, pi = i_lo + lane - pc.
+// pj = j_lo + lane - pc, pi = i_lo + lane - pc. Per batch of 32 staged rays a
+// warp vote picks a loop without the per-ray type test when all of them are
+// x-driven (or all y-driven), the usual case away from the 45-degree directions.
 template <bool MIRROR, class Stage>
 __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const Stage &load, int c0,
                                                int c1, float pj, float pi, int i_lo, int j_lo, int lane)
@@ -249,33 +251,49 @@ __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const 
     // x-driven rays: this lane's column; y-driven rays: this lane's row
     const unsigned col_x = acc0 + 4u * (unsigned)(MIRROR ? (kTile - 1) - lane : lane);
     const unsigned row_y = acc0 + 4u * (unsigned)(lane * kAccStride);
+    auto x_step = [&](const float4 &r) { // x-driven: this lane's column, rows a and a+1
+        float f;
+        const int a = floor_frac(fmaf(r.y, pj, r.x), f) - i_lo;
+        const float w1 = f * r.z, w0 = r.z - w1;
+        const unsigned ad = col_x + 4u * (unsigned)(a * kAccStride);
+        if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+        if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u * kAccStride, w1);
+    };
+    auto y_step = [&](const float4 &r) { // y-driven: this lane's row, columns a and a+1
+        float f;
+        const int a = floor_frac(fmaf(r.y, pi, r.x), f) - j_lo;
+        const float w1 = f * r.z, w0 = r.z - w1;
+        if (MIRROR) {
+            const unsigned ad = row_y + 4u * (unsigned)((kTile - 1) - a);
+            if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+            if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad - 4u, w1);
+        } else {
+            const unsigned ad = row_y + 4u * (unsigned)a;
+            if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+            if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u, w1);
+        }
+    };
     for (int cb = c0; cb <= c1; cb += 32) {
         const int c = cb + lane;
-        if (c <= c1) stage[lane] = load(c);
+        bool xd = true, yd = true; // lanes past c1 stage nothing and agree with both
+        if (c <= c1) {
+            const float4 r = load(c);
+            stage[lane] = r;
+            xd = r.w > 0.5f;
+            yd = !xd;
+        }
+        const bool all_x = __all_sync(0xffffffffu, xd), all_y = __all_sync(0xffffffffu, yd);
         __syncwarp();
         const int cnt = min(32, c1 - cb + 1);
-        for (int t = 0; t < cnt; ++t) {
-            const float4 r = stage[t];
-            if (r.w > 0.5f) { // x-driven: this lane's column, rows a and a+1
-                float f;
-                const int a = floor_frac(fmaf(r.y, pj, r.x), f) - i_lo;
-                const float w1 = f * r.z, w0 = r.z - w1;
-                const unsigned ad = col_x + 4u * (unsigned)(a * kAccStride);
-                if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
-                if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u * kAccStride, w1);
-            } else {          // y-driven: this lane's row, columns a and a+1
-                float f;
-                const int a = floor_frac(fmaf(r.y, pi, r.x), f) - j_lo;
-                const float w1 = f * r.z, w0 = r.z - w1;
-                if (MIRROR) {
-                    const unsigned ad = row_y + 4u * (unsigned)((kTile - 1) - a);
-                    if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
-                    if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad - 4u, w1);
-                } else {
-                    const unsigned ad = row_y + 4u * (unsigned)a;
-                    if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
-                    if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u, w1);
-                }
+        if (all_x) {
+            for (int t = 0; t < cnt; ++t) x_step(stage[t]);
+        } else if (all_y) {
+            for (int t = 0; t < cnt; ++t) y_step(stage[t]);
+        } else {
+            for (int t = 0; t < cnt; ++t) {
+                const float4 r = stage[t];
+                if (r.w > 0.5f) x_step(r);
+                else y_step(r);
             }
         }
         __syncwarp();
