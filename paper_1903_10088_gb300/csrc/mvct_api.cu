@@ -95,12 +95,13 @@ int validate(const mvct_geometry *g, int S)
 
 // Ray and view tables in FP64, stored as FP32 (layout in mvct_device.cuh).
 void build_tables(const mvct_geometry &g, int S, std::vector<float4> &rays, std::vector<float4> &views,
-                  Geo &geo)
+                  std::vector<int> &ranges, Geo &geo)
 {
     const int n = g.n, V = g.n_views, C = g.n_channels;
     const double delta = g.fov_cm / n, pc = (n - 1) / 2.0;
     const double dg = fan_of(g) / C;
     rays.resize((size_t)V * C);
+    ranges.resize((size_t)V * C);
     views.resize(V);
     for (int v = 0; v < V; ++v) {
         const double b = g.view0_rad + 2.0 * kPi * v / V;
@@ -120,6 +121,21 @@ void build_tables(const mvct_geometry &g, int S, std::vector<float4> &rays, std:
                 r = make_float4((float)((sx - sy * m) / delta + pc), (float)m, (float)(delta / std::fabs(dy)), 0.f);
             }
             rays[(size_t)v * C + c] = r;
+            // samples whose taps can fall inside the image, u(p) in (-1, n), from the
+            // stored FP32 u_c and m, widened by one sample on each side (a superset:
+            // taps outside land on the zero rows)
+            const double uc = r.x, mm = r.y;
+            int p_lo = 0, p_hi = n - 1;
+            if (mm != 0.0) {
+                const double a = (-1.0 - uc) / mm, bb = ((double)n - uc) / mm;
+                const double lo = std::max(std::min(a, bb) + pc, -2.0), hi = std::min(std::max(a, bb) + pc, n + 1.0);
+                p_lo = std::max(0, (int)std::floor(lo) - 1);
+                p_hi = std::min(n - 1, (int)std::ceil(hi) + 1);
+            } else if (!(uc > -1.0 && uc < (double)n)) {
+                p_hi = -1;
+            }
+            if (p_hi < p_lo) p_lo = 0, p_hi = -1;
+            ranges[(size_t)v * C + c] = p_lo | ((p_hi + 1) << 16);
         }
     }
     geo.n = n;
@@ -136,7 +152,7 @@ void build_tables(const mvct_geometry &g, int S, std::vector<float4> &rays, std:
 void free_plan(mvct_plan_s *P)
 {
     if (!P) return;
-    void *ptrs[] = {P->rays, P->views, P->a1t, P->a1, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
+    void *ptrs[] = {P->rays, P->ray_range, P->views, P->a1t, P->a1, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
                     P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
                     P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched,
                     P->d_slice, P->d_group, P->d_block_group, P->d_count, P->fbp_g, P->fbp_cos, P->fbp_q, P->sorder,
@@ -168,7 +184,8 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     CK(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, P->device));
 
     std::vector<float4> rays, views;
-    build_tables(*g, n_subsets, rays, views, P->geo);
+    std::vector<int> ranges;
+    build_tables(*g, n_subsets, rays, views, ranges, P->geo);
     const size_t nn = (size_t)g->n * g->n, R = (size_t)g->n_views * g->n_channels;
     const size_t Rs = (size_t)P->geo.Vs * g->n_channels;
     P->reduce_grid = P->num_sms * 8;
@@ -185,6 +202,7 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     const size_t n_flags = (size_t)P->n_tiles * P->groups_cap;
 
     bool ok = cudaMalloc(&P->rays, R * sizeof(float4)) == cudaSuccess &&
+              cudaMalloc(&P->ray_range, R * sizeof(int)) == cudaSuccess &&
               cudaMalloc(&P->views, g->n_views * sizeof(float4)) == cudaSuccess &&
               cudaMalloc(&P->a1t, nn * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&P->a1, R * sizeof(float)) == cudaSuccess &&
@@ -218,6 +236,7 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     }
     cudaStream_t st = 0;
     cudaError_t e = cudaMemcpy(P->rays, rays.data(), R * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(P->ray_range, ranges.data(), R * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->views, views.data(), g->n_views * sizeof(float4), cudaMemcpyHostToDevice);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaMemset(P->pad[k], 0, pad_floats(g->n) * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(P->pad_ones, 0, pad_floats(g->n) * sizeof(float));

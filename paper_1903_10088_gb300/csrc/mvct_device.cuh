@@ -112,25 +112,18 @@ constexpr int kPadRows = 2;
 // the rows of img, which are the columns of imgT, so reading imgT keeps the
 // warp's accesses contiguous. RO selects read-only-cache loads (only legal when
 // the image is not written during the kernel). TS is the stored element type
-// (FP32, BF16 or FP16); taps are widened to FP32 and the sum is FP32.
+// (FP32, BF16 or FP16); taps are widened to FP32 and the sum is FP32. range
+// packs the samples p_lo .. p_hi the ray walks (those whose taps can fall inside
+// the image, widened by one; taps outside land on the zero rows), computed on
+// the host with the plan's ray table: p_lo | (p_hi + 1) << 16.
 template <bool RO, typename TS = float>
 __device__ __forceinline__ float joseph_warp(const TS *img, const TS *imgT, int n, float pc,
-                                             float4 r, int lane)
+                                             float4 r, int range, int lane)
 {
     // img / imgT point at row 0 of zero-row-padded buffers (see kPadRows)
     const TS *src = (r.w > 0.5f) ? img : imgT;
     const float uc = r.x, m = r.y;
-    // Samples whose taps can fall inside the image: u(p) in (-1, n), widened by
-    // one sample (taps outside land on the zero rows).
-    int p_lo = 0, p_hi = n - 1;
-    if (m != 0.f) {
-        float a = __fdividef(-1.f - uc, m), b = __fdividef((float)n - uc, m);
-        float lo = fmaxf(fminf(a, b) + pc, -2.f), hi = fminf(fmaxf(a, b) + pc, (float)n + 1.f);
-        p_lo = max(0, (int)floorf(lo) - 1);
-        p_hi = min(n - 1, (int)ceilf(hi) + 1);
-    } else if (!(uc > -1.f && uc < (float)n)) {
-        p_hi = -1;
-    }
+    const int p_lo = range & 0xffff, p_hi = (range >> 16) - 1;
     const int rmin = -kPadRows, rmax = n + kPadRows - 2;
     // Four samples per lane per step, all eight taps loaded before use.
     constexpr int U = 4;

@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(kThreads) k_pad_transpose(const float *__restr
 // One warp per ray (grid-stride). out[k*C + c] = (A img)_(v_k, c) * mul[v_k*C + c]
 // (mul optional). check_p/data_err: set-up validation of p and w.
 __global__ void __launch_bounds__(kThreads)
-k_forward(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img,
+k_forward(Geo g, const float4 *__restrict__ rays, const int *__restrict__ ranges, const float *__restrict__ img,
           const float *__restrict__ imgT, float *__restrict__ out, int subset, int rows,
           const float *__restrict__ mul, const float *__restrict__ check_p, int *data_err)
 {
@@ -46,7 +46,7 @@ k_forward(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img,
         const int v = subset < 0 ? k : subset + k * g.S;
         const size_t rv = (size_t)v * g.C + c;
         const float4 r = __ldg(&rays[rv]);
-        float q = joseph_warp<true>(img, imgT, g.n, g.pc, r, lane);
+        float q = joseph_warp<true>(img, imgT, g.n, g.pc, r, __ldg(ranges + rv), lane);
         if (lane == 0) {
             if (mul) {
                 const float wv = __ldg(mul + rv);
@@ -78,7 +78,7 @@ k_weight_a1(const float *__restrict__ a1, const float *__restrict__ w, const flo
 
 // Per-block FP64 sum of w * (A img - p)^2 over all views (one warp per ray).
 __global__ void __launch_bounds__(kThreads)
-k_residual(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img,
+k_residual(Geo g, const float4 *__restrict__ rays, const int *__restrict__ ranges, const float *__restrict__ img,
            const float *__restrict__ imgT, const float *__restrict__ p, const float *__restrict__ w,
            double *__restrict__ partials)
 {
@@ -87,7 +87,7 @@ k_residual(Geo g, const float4 *__restrict__ rays, const float *__restrict__ img
     const int total = g.V * g.C;
     double acc = 0.0;
     for (int ray = blockIdx.x * kWarps + warp; ray < total; ray += gridDim.x * kWarps) {
-        const float q = joseph_warp<true>(img, imgT, g.n, g.pc, __ldg(&rays[ray]), lane);
+        const float q = joseph_warp<true>(img, imgT, g.n, g.pc, __ldg(&rays[ray]), __ldg(ranges + ray), lane);
         const double r = (double)q - (double)__ldg(p + ray);
         acc += (double)__ldg(w + ray) * r * r;
     }
@@ -251,7 +251,7 @@ cudaError_t launch_forward(const mvct_plan_s *P, const float *img, const float *
 {
     const int rows = rows_of(P, subset);
     k_forward<<<ray_grid(P, (long long)rows * P->geo.C), kThreads, 0, st>>>(
-        P->geo, P->rays, img, imgT, out, subset, rows, mul, check_p, data_err);
+        P->geo, P->rays, P->ray_range, img, imgT, out, subset, rows, mul, check_p, data_err);
     return cudaGetLastError();
 }
 
@@ -267,7 +267,7 @@ cudaError_t launch_weight_a1(const mvct_plan_s *P, const float *w, const float *
 cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float *imgT,
                             const float *p, const float *w, double *partials, cudaStream_t st)
 {
-    k_residual<<<P->reduce_grid, kThreads, 0, st>>>(P->geo, P->rays, img, imgT, p, w, partials);
+    k_residual<<<P->reduce_grid, kThreads, 0, st>>>(P->geo, P->rays, P->ray_range, img, imgT, p, w, partials);
     return cudaGetLastError();
 }
 

@@ -13,6 +13,7 @@ namespace mvct {
 struct SliceDesc {
     Geo g;
     const float4 *rays;
+    const int *ray_range;     // [V*C] p_lo | (p_hi + 1) << 16 (see joseph_warp)
     const float4 *views;
     const float *p;           // measured log projections [V][C]
     const float *w;           // statistical weights [V][C]
@@ -79,6 +80,7 @@ struct mvct_plan_s {
     mvct::Geo geo{};
 
     float4 *rays = nullptr;     // [V*C] ray table (see mvct_device.cuh)
+    int *ray_range = nullptr;   // [V*C] samples walked by each ray: p_lo | (p_hi + 1) << 16
     float4 *views = nullptr;    // [V] source point and central direction
     float *a1t = nullptr;       // [n*n] A^T 1 over all views (support mask = a1t > 0)
     float *a1 = nullptr;        // [V*C] A 1 (projection of the all-ones image), geometry only

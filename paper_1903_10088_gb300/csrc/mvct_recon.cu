@@ -120,11 +120,13 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             const int gw0 = lb * kWarps + warp, GW = grp.nblocks * kWarps;
             // the next ray's table entry and data are fetched while this ray is walked
             float4 r_nx = make_float4(0.f, 0.f, 0.f, 1.f);
+            int range_nx = 0;
             float p_nx = 0.f, w_nx = 0.f;
             if (gw0 < Rs) {
                 const int k = gw0 / g.C;
                 const size_t rv = (size_t)(s + k * g.S) * g.C + (gw0 - k * g.C);
                 r_nx = __ldg(&rays[rv]);
+                range_nx = __ldg(sd.ray_range + rv);
                 if (lane == 0) {
                     p_nx = ldv<true>(pp + rv);
                     w_nx = ldv<true>(ww + rv);
@@ -132,18 +134,20 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             }
             for (int ray = gw0; ray < Rs; ray += GW) {
                 const float4 r = r_nx;
+                const int range = range_nx;
                 const float pv = p_nx, wv = w_nx;
                 const int nray = ray + GW;
                 if (nray < Rs) {
                     const int k = nray / g.C;
                     const size_t rv = (size_t)(s + k * g.S) * g.C + (nray - k * g.C);
                     r_nx = __ldg(&rays[rv]);
+                    range_nx = __ldg(sd.ray_range + rv);
                     if (lane == 0) {
                         p_nx = ldv<true>(pp + rv);
                         w_nx = ldv<true>(ww + rv);
                     }
                 }
-                const float q_ray = joseph_warp<false, TS>(pcur, pcurT, g.n, g.pc, r, lane);
+                const float q_ray = joseph_warp<false, TS>(pcur, pcurT, g.n, g.pc, r, range, lane);
                 if (lane == 0) {
                     const float res = q_ray - pv;
                     const float ev = a.poisson ? wv - expf(-q_ray) : wv * res;
@@ -593,6 +597,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     std::memset(&sd, 0, sizeof(sd));
     sd.g = g;
     sd.rays = P->rays;
+    sd.ray_range = P->ray_range;
     sd.views = P->views;
     sd.p = d_sino;
     sd.w = d_weights;
@@ -936,6 +941,7 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
         std::memset(&sd, 0, sizeof(sd));
         sd.g = P->geo;
         sd.rays = P->rays;
+        sd.ray_range = P->ray_range;
         sd.views = P->views;
         sd.p = d_sinos[i];
         sd.w = d_weights[i];
