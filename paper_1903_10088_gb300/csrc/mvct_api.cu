@@ -226,7 +226,7 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
               cudaMalloc(&P->d_slice, sizeof(SliceDesc)) == cudaSuccess &&
               cudaMalloc(&P->d_group, sizeof(GroupDesc)) == cudaSuccess &&
               cudaMalloc(&P->d_block_group, sizeof(int) * std::max(1, P->recon_grid)) == cudaSuccess &&
-              cudaMalloc(&P->d_count, 128) == cudaSuccess &&
+              cudaMalloc(&P->d_count, sizeof(unsigned int) * kGroupSyncWords) == cudaSuccess &&
               cudaMalloc(&P->sorder, sizeof(int) * std::max(1, n_subsets)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();

@@ -462,6 +462,12 @@ __device__ __forceinline__ void add_release(unsigned int *p, unsigned int v)
 
 __device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
+// Start moving the 128-byte line holding p into this SM's L1 (no register result).
+__device__ __forceinline__ void prefetch_l1(const void *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // Barrier number k (0, 1, 2, ... counted identically by every block) among the
 // nblocks blocks that share `count`: each block adds one arrival with release
 // semantics and polls (relaxed) until the counter reaches (k+1)*nblocks + extra,

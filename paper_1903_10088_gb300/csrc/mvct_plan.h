@@ -39,10 +39,26 @@ struct SliceDesc {
 };
 
 // A group of consecutive blocks that reconstructs a list of slices in turn.
+// Each block group owns kGroupSyncWords words of device memory, two 128-byte
+// lines: its barrier counter (word 0 of the first line) and the publication of
+// Phi_n by the group's reducer block (PhiPub, the second line).
+constexpr int kGroupSyncWords = 64;
+struct PhiPub {
+    unsigned int stamp;       // barrier count after which phi and pass are valid
+    unsigned int pad;
+    double phi;               // Phi_n
+    double pass;              // Phi_{n-S+1} + ... + Phi_n
+};
+static_assert(sizeof(PhiPub) <= 128, "PhiPub fits one line");
+inline __host__ __device__ PhiPub *phi_pub(unsigned int *count)
+{
+    return reinterpret_cast<PhiPub *>(count + 32);
+}
+
 struct GroupDesc {
     int block0, nblocks;      // blocks [block0, block0 + nblocks)
     int slice0, nslices;      // slices [slice0, slice0 + nslices) of the slice array
-    unsigned int *count;      // the group's barrier counter (own 128-byte line)
+    unsigned int *count;      // the group's barrier counter and PhiPub (kGroupSyncWords words)
     double *partials;         // [nblocks] FP64 partial sums of Phi
 };
 
@@ -111,7 +127,7 @@ struct mvct_plan_s {
     mvct::SliceDesc *d_slice = nullptr; // the one-slice launch description
     mvct::GroupDesc *d_group = nullptr;
     int *d_block_group = nullptr;       // [recon_grid] zeros
-    unsigned int *d_count = nullptr;    // group barrier counter
+    unsigned int *d_count = nullptr;    // group barrier counter and PhiPub (kGroupSyncWords words)
     bool in_batch = false;              // owned by a batch (its scratch is in use there)
     // 16-bit storage buffers (allocated on first use): padded ping-pong image
     // copies and transposes, p and w

@@ -9,9 +9,11 @@
 //            residual r = q - p, prescaled weighted residual e = scale*w*r,
 //            FP64 partial sums of r^2 per block
 //   barrier
-//   lambda   every block of the group reduces the partials in the same fixed
-//            order, so every block derives the same Phi_n, lambda_n (Eq. 4-5)
-//            and best-iterate decision without another barrier
+//   lambda   a block without a phase-B item reduces the partials in a fixed
+//            order and publishes Phi_n (a flag, no barrier); every block derives
+//            the same lambda_n (Eq. 4-5) and best-iterate decision from it when
+//            its first update needs it (with no such block, every block reduces
+//            the partials itself, in the same order)
 //   phase B  32x32 pixel tiles: splat of the matched backprojection of e (view
 //            groups of one tile merged in group order), TV_eps gradient,
 //            surrogate-preconditioned step, clamp at 0, write mu^(n+1) and its
@@ -57,6 +59,7 @@ __device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int
 struct LoopShared {
     double warp[kWarps];
     double lambda, phi_prev, best_pass;
+    double phi_n, pass_n;          // Phi_n and the pass sum of the current sub-iteration
     long long best_n;
     float tau;
     int best_flag, ok;
@@ -174,38 +177,59 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         }
 
         // ---- adaptive lambda (Eq. 4-5) and best iterate (Sec. 4.2) ------
-        // Every block sums the group's partials in the same fixed order.
-        {
-            constexpr int L = (MVCT_MAX_RECON_GRID + kThreads - 1) / kThreads;
-            double v[L];
+        // Only the update of phase B needs lambda. If the group has a block
+        // without a phase-B item, that block (the reducer) sums the partials
+        // right away and publishes Phi_n and the pass sum; the other blocks read
+        // them when their first update needs them. Otherwise every block sums the
+        // partials itself after its first splat. Either way the sums are taken in
+        // the same fixed order, so every block derives the same lambda_n and
+        // best-iterate decision.
+        const int slot_n = (int)(n % g.S);
+        const bool full = n >= g.S - 1;
+        const int n_items_all = sd.n_tiles * sd.groups;
+        const int reducer = n_items_all < grp.nblocks ? n_items_all : -1;
+        PhiPub *pub = phi_pub(grp.count);
+        const unsigned int pub_stamp = bk;
+        // all threads: Phi_n and the pass sum Phi_{n-S+1} + ... + Phi_n into sh
+        auto reduce_phi = [&]() {
+            {
+                constexpr int L = (MVCT_MAX_RECON_GRID + kThreads - 1) / kThreads;
+                double v[L];
 #pragma unroll
-            for (int u = 0; u < L; ++u) {
-                const unsigned int b = threadIdx.x + u * kThreads;
-                v[u] = b < (unsigned int)grp.nblocks ? grp.partials[b] : 0.0;
+                for (int u = 0; u < L; ++u) {
+                    const unsigned int b = threadIdx.x + u * kThreads;
+                    v[u] = b < (unsigned int)grp.nblocks ? grp.partials[b] : 0.0;
+                }
+                double t = 0.0;
+#pragma unroll
+                for (int u = 0; u < L; ++u) t += v[u];
+                t = warp_sum(t);
+                if (lane == 0) sh.warp[warp] = t;
             }
-            double t = 0.0;
-#pragma unroll
-            for (int u = 0; u < L; ++u) t += v[u];
-            t = warp_sum(t);
-            if (lane == 0) sh.warp[warp] = t;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double phi = 0.0;
-            for (int k = 0; k < kWarps; ++k) phi += sh.warp[k];
-            // the last S values of Phi live in the slice's state (global memory):
-            // block 0 of the group writes slot n mod S; every block reads the
-            // other slots (written in earlier sub-iterations, ordered by the group
-            // barriers; read past L1) and uses its own Phi_n for slot n mod S
-            const int slot_n = (int)(n % g.S);
-            if (lane == 0 && lb == 0) st->phi_ring[slot_n] = phi;
-            // pass sum Phi_{n-S+1} + ... + Phi_n: lane-strided, then the warp tree
-            double pass = 0.0;
-            const bool full = n >= g.S - 1;
-            if (full)
-                for (int k = lane; k < g.S; k += 32) pass += (k == slot_n) ? phi : __ldcg(st->phi_ring + k);
-            pass = warp_sum(pass);
-            if (lane == 0) {
+            __syncthreads();
+            if (warp == 0) {
+                double phi = 0.0;
+                for (int k = 0; k < kWarps; ++k) phi += sh.warp[k];
+                // the last S values of Phi live in the slice's state (global
+                // memory): the reducer (block 0 without one) writes slot n mod S;
+                // the other slots were written in earlier sub-iterations, ordered
+                // by the group barriers
+                if (lane == 0 && lb == (reducer >= 0 ? reducer : 0)) st->phi_ring[slot_n] = phi;
+                double pass = 0.0;
+                if (full)
+                    for (int k = lane; k < g.S; k += 32) pass += (k == slot_n) ? phi : st->phi_ring[k];
+                pass = warp_sum(pass);
+                if (lane == 0) {
+                    sh.phi_n = phi;
+                    sh.pass_n = pass;
+                }
+            }
+            __syncthreads();
+        };
+        // Eq. 4-5 and the best-iterate decision from sh.phi_n, sh.pass_n
+        auto apply_lambda = [&]() {
+            if (threadIdx.x == 0) {
+                const double phi = sh.phi_n, pass = sh.pass_n;
                 double lam;
                 if (sd.sched) {
                     lam = sd.sched[it];
@@ -232,8 +256,42 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                     sd.lam_hist[it] = lam;
                 }
             }
+            __syncthreads();
+        };
+        // lambda_n in this block: from the reducer's publication, or reduced here.
+        // False if the wait for the publication gave up.
+        auto obtain_lambda = [&]() -> bool {
+            if (reducer < 0) {
+                reduce_phi();
+            } else {
+                if (threadIdx.x == 0) {
+                    const bool ok = wait_flag(&pub->stamp, pub_stamp, err, a.timeout_ns, a.spin_cap);
+                    if (ok) {
+                        sh.phi_n = __ldcg(&pub->phi);
+                        sh.pass_n = __ldcg(&pub->pass);
+                    }
+                    sh.ok = ok;
+                }
+                __syncthreads();
+                if (!sh.ok) return false;
+            }
+            apply_lambda();
+            return true;
+        };
+        if (lb == reducer) {
+            reduce_phi();
+            if (threadIdx.x == 0) {
+                pub->phi = sh.phi_n;
+                pub->pass = sh.pass_n;
+                st_release(&pub->stamp, pub_stamp);
+            }
+            apply_lambda();
+        } else if (reducer < 0) {
+            // every block reduces: start moving the partials and the ring into L1
+            for (int b = threadIdx.x * 16; b < grp.nblocks; b += kThreads * 16) prefetch_l1(grp.partials + b);
+            if (full && threadIdx.x * 16 < g.S) prefetch_l1(st->phi_ring + threadIdx.x * 16);
         }
-        __syncthreads();
+        bool lam_done = lb == reducer;
 
         // ---- phase B: tile splat (estimation) + TV + preconditioned step
         // Items: (tile t, view group h), group h holding the subset rows
@@ -241,9 +299,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         // H-1 (the owner) adds the partials in group order and updates the
         // tile. Non-owner items come first in every block's sequence, so an
         // owner only ever waits on items that never wait.
-        const float tau = sh.tau;
         float *best = sd.best;
-        const bool keep_best = sh.best_flag && best;
         const int H = sd.groups;
         const int n_items = sd.n_tiles * H, n_nonowner = sd.n_tiles * (H - 1);
         const int C = g.C;
@@ -272,6 +328,12 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 __syncthreads(); // sh.acc is zeroed by the next item
                 continue;
             }
+            if (!lam_done) {
+                if (!obtain_lambda()) return false;
+                lam_done = true;
+            }
+            const float tau = sh.tau;
+            const bool keep_best = sh.best_flag && best;
 
             if (threadIdx.x == 0) {
                 bool ok = true;
@@ -332,6 +394,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             }
             __syncthreads(); // tile (sh.acc[0]) is zeroed by the next item
         }
+        if (!lam_done && !obtain_lambda()) return false; // blocks without an owner item keep the same state
         if (!group_sync(grp.count, err, bk, grp.nblocks, 0u, a.timeout_ns, a.spin_cap)) return false;
         ++bk;
         if (timer) {
@@ -635,7 +698,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     if (o.subset_order)
         CK(cudaMemcpyAsync(P->sorder, o.subset_order, sizeof(int) * P->geo.S, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(P->bar, 0, sizeof(Barrier), st));
-    CK(cudaMemsetAsync(P->d_count, 0, 128, st));
+    CK(cudaMemsetAsync(P->d_count, 0, sizeof(unsigned int) * kGroupSyncWords, st));
     CK(cudaMemsetAsync(P->phase_ns, 0, 2 * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(P->tile_flag, 0, sizeof(unsigned int) * (size_t)P->n_tiles * P->groups_cap, st));
 
@@ -743,7 +806,7 @@ struct mvct_batch_s {
     SliceDesc *d_slices = nullptr;
     GroupDesc *d_groups = nullptr;
     int *d_block_group = nullptr;
-    unsigned int *d_counts = nullptr;   // [ngroups][32]
+    unsigned int *d_counts = nullptr;   // [ngroups][kGroupSyncWords]
     double *d_partials = nullptr;       // [grid]
     Barrier *d_bar = nullptr;
     unsigned long long *d_phase = nullptr;
@@ -863,7 +926,7 @@ extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_bat
     bool ok = cudaMalloc(&b->d_slices, sizeof(SliceDesc) * count) == cudaSuccess &&
               cudaMalloc(&b->d_groups, sizeof(GroupDesc) * b->ngroups) == cudaSuccess &&
               cudaMalloc(&b->d_block_group, sizeof(int) * G) == cudaSuccess &&
-              cudaMalloc(&b->d_counts, 128 * (size_t)b->ngroups) == cudaSuccess &&
+              cudaMalloc(&b->d_counts, sizeof(unsigned int) * kGroupSyncWords * (size_t)b->ngroups) == cudaSuccess &&
               cudaMalloc(&b->d_partials, sizeof(double) * G) == cudaSuccess &&
               cudaMalloc(&b->d_bar, sizeof(Barrier)) == cudaSuccess &&
               cudaMalloc(&b->d_phase, 2 * sizeof(unsigned long long)) == cudaSuccess &&
@@ -874,7 +937,7 @@ extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_bat
         return mvct_fail(MVCT_ENOMEM, "mvct_batch_create: device allocation failed");
     }
     for (int gi = 0; gi < b->ngroups; ++gi) {
-        groups[gi].count = b->d_counts + 32 * gi;
+        groups[gi].count = b->d_counts + kGroupSyncWords * gi;
         groups[gi].partials = b->d_partials + groups[gi].block0;
     }
     b->h_groups = groups;
@@ -983,7 +1046,7 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
     const mvct_recon_opts &o = b->opts;
     CK(cudaEventRecord(b->ev[0], st));
     CK(cudaMemsetAsync(b->d_bar, 0, sizeof(Barrier), st));
-    CK(cudaMemsetAsync(b->d_counts, 0, 128 * (size_t)b->ngroups, st));
+    CK(cudaMemsetAsync(b->d_counts, 0, sizeof(unsigned int) * kGroupSyncWords * (size_t)b->ngroups, st));
     CK(cudaMemsetAsync(b->d_phase, 0, 2 * sizeof(unsigned long long), st));
     k_state_init<<<std::min(b->count, 1024), 256, 0, st>>>(b->d_states, b->count, o.lambda0);
     CK(cudaGetLastError());
