@@ -397,7 +397,10 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(WORKLOAD, l2="flushed between timed steps (512 MiB write)",
                        parallelism=f"replicas x{ws}, one slice per GPU per step",
-                       launch_shape={"view_groups_per_tile": tune["groups"], "grid_blocks": tune["grid_blocks"],
+                       launch_shape={"view_groups_per_tile": tune["groups"] or "default rule (balanced plan)",
+                                     "grid_blocks": tune["grid_blocks"],
+                                     "candidates": [[c["groups"], c["grid_blocks"], round(c["ms_per_iter"], 5)]
+                                                    for c in tune["candidates"]],
                                      "autotuned_ms_per_iter": tune["ms_per_iter"],
                                      "default_ms_per_iter": tune["default_ms_per_iter"]}),
         "gray_per_s": gray, "loop_ms_per_slice": float(np.mean(loop_ms)),

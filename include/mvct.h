@@ -295,7 +295,8 @@ int mvct_tv_grad_noalloc(const float *d_img, int32_t n, double eps, float *d_gra
  * order of the groups' partial tiles. */
 #define MVCT_TUNE_MAX 32
 typedef struct mvct_tune_report {
-    int32_t groups;              /* chosen view groups per tile (batch: 0 = the default rule) */
+    int32_t groups;              /* chosen view groups per tile (0 = the default rule: for one slice the
+                                    balanced plan where the sizes allow it, see mvct_plan_set_shape) */
     int32_t grid_blocks;         /* chosen blocks of the loop launch */
     double ms_per_iter;          /* loop time per sub-iteration of the choice */
     double default_ms_per_iter;  /* the same for the untuned default */
@@ -317,7 +318,13 @@ int mvct_plan_tune(mvct_plan plan, const float *d_sino, const float *d_weights, 
 /* Set the one-slice launch shape explicitly (e.g. a shape an earlier
  * mvct_plan_tune reported): groups = view groups per tile (0 = the default
  * rule, at most min(8, views per subset)), grid_blocks = blocks of the loop
- * launch (0 = every co-resident block). MVCT_EINVAL outside those ranges. */
+ * launch (0 = every co-resident block). MVCT_EINVAL outside those ranges.
+ * The default rule with every co-resident block uses the balanced plan where
+ * the sizes allow it (r blocks per SM, 2 <= r: r - 1 items of half a tile's
+ * views per SM and one item of a tile split into 2..8 groups, one block left
+ * for the reduction of Phi; e.g. 512^2 with 40 views per subset on 152 SMs);
+ * otherwise every tile is split into min(8, views per subset, blocks / tiles)
+ * groups. A groups value > 0 always splits every tile into that many groups. */
 int mvct_plan_set_shape(mvct_plan plan, int32_t groups, int32_t grid_blocks);
 
 /* Tune a bound batch: the view groups per tile of every slice (the default

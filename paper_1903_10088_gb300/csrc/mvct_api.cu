@@ -156,7 +156,7 @@ void free_plan(mvct_plan_s *P)
                     P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
                     P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched,
                     P->d_slice, P->d_group, P->d_block_group, P->d_count, P->fbp_g, P->fbp_cos, P->fbp_q, P->sorder,
-                    P->pad16[0], P->pad16[1], P->pad16[2], P->pad16[3], P->p16, P->w16};
+                    P->pad16[0], P->pad16[1], P->pad16[2], P->pad16[3], P->p16, P->w16, P->bitems};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete P;
@@ -198,6 +198,9 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     P->groups_cap = std::max(1, std::min(kMaxGroups, P->geo.Vs));
     P->groups = std::max(1, std::min(P->groups_cap, P->recon_grid / P->n_tiles));
     P->grid = P->recon_grid;
+    std::vector<int4> bitems;
+    const bool balanced = balanced_items(P->n_tiles, P->geo.Vs, P->groups_cap, P->recon_grid, P->num_sms, bitems,
+                                         P->bitems_reducer);
     const size_t part_floats = (size_t)P->n_tiles * P->groups_cap * kTile * kTile;
     const size_t n_flags = (size_t)P->n_tiles * P->groups_cap;
 
@@ -227,7 +230,8 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
               cudaMalloc(&P->d_group, sizeof(GroupDesc)) == cudaSuccess &&
               cudaMalloc(&P->d_block_group, sizeof(int) * std::max(1, P->recon_grid)) == cudaSuccess &&
               cudaMalloc(&P->d_count, sizeof(unsigned int) * kGroupSyncWords) == cudaSuccess &&
-              cudaMalloc(&P->sorder, sizeof(int) * std::max(1, n_subsets)) == cudaSuccess;
+              cudaMalloc(&P->sorder, sizeof(int) * std::max(1, n_subsets)) == cudaSuccess &&
+              (!balanced || cudaMalloc(&P->bitems, sizeof(int4) * P->recon_grid) == cudaSuccess);
     if (!ok) {
         cudaGetLastError();
         free_plan(P);
@@ -238,6 +242,8 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
     cudaError_t e = cudaMemcpy(P->rays, rays.data(), R * sizeof(float4), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->ray_range, ranges.data(), R * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(P->views, views.data(), g->n_views * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && balanced)
+        e = cudaMemcpy(P->bitems, bitems.data(), sizeof(int4) * P->recon_grid, cudaMemcpyHostToDevice);
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaMemset(P->pad[k], 0, pad_floats(g->n) * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(P->pad_ones, 0, pad_floats(g->n) * sizeof(float));
     if (e == cudaSuccess) e = launch_fill(pad_row0(P->pad_ones, g->n), nn, 1.f, st);

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "mvct.h"
 #include "mvct_device.cuh"
 
@@ -35,6 +37,11 @@ struct SliceDesc {
     const int *sorder;        // [S] subset visiting order (or null: 0, 1, ..., S-1)
     mvct_recon_state *st;     // loop state (resume in, final out)
     int tiles_x, n_tiles, groups;
+    // balanced phase-B plan (or null: every tile in `groups` groups): per block
+    // of the group (tile, view group h, view groups of the tile, first partial
+    // slot of the tile), tile -1 for a block without an item
+    const int4 *bitems;
+    int reducer;              // block that reduces and publishes Phi_n (-1: every block)
     float beta;
 };
 
@@ -117,6 +124,8 @@ struct mvct_plan_s {
     int groups_cap = 1;            // partial-tile buffers allocated for this many groups
     int tuned_groups = 0;          // > 0: view groups chosen by the autotuner (overrides `groups`)
     int grid = 0;                  // blocks of one-slice loop launches (<= recon_grid; autotuner)
+    int4 *bitems = nullptr;        // [recon_grid] balanced phase-B plan of the default shape (or null)
+    int bitems_reducer = -1;       // its block without an item
     double *partials = nullptr; // [partials_cap] per-block FP64 partial sums
     double *partials2 = nullptr;
     int partials_cap = 0;
@@ -184,6 +193,14 @@ int recon_occupancy(mvct_plan_s *P);
 // View groups per tile for a group of nblocks blocks; `override_h` > 0 forces
 // that count (autotuner), clamped to the plan's buffers and its views per subset.
 int slice_groups(const mvct_plan_s *P, int nblocks, int override_h = 0);
+
+// Balanced phase-B plan of a one-slice launch of `grid` blocks on num_sms SMs
+// (block b assumed on SM b mod num_sms): every SM gets r - 1 items of half a
+// tile's views (r = grid / num_sms blocks per SM) and one small item of a tile
+// split into 2..groups_cap groups; one block stays without an item. False (and
+// nothing written) when the sizes do not allow it.
+bool balanced_items(int n_tiles, int Vs, int groups_cap, int grid, int num_sms, std::vector<int4> &items,
+                    int &idle_block);
 
 } // namespace mvct
 

@@ -186,8 +186,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         // best-iterate decision.
         const int slot_n = (int)(n % g.S);
         const bool full = n >= g.S - 1;
-        const int n_items_all = sd.n_tiles * sd.groups;
-        const int reducer = n_items_all < grp.nblocks ? n_items_all : -1;
+        const int reducer = sd.reducer;
         PhiPub *pub = phi_pub(grp.count);
         const unsigned int pub_stamp = bk;
         // all threads: Phi_n and the pass sum Phi_{n-S+1} + ... + Phi_n into sh
@@ -294,29 +293,25 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         bool lam_done = lb == reducer;
 
         // ---- phase B: tile splat (estimation) + TV + preconditioned step
-        // Items: (tile t, view group h), group h holding the subset rows
-        // h, h + H, h + 2H, ... Groups h < H-1 publish a partial tile; group
-        // H-1 (the owner) adds the partials in group order and updates the
-        // tile. Non-owner items come first in every block's sequence, so an
-        // owner only ever waits on items that never wait.
+        // Item (tile t, view group h of the tile's Ht groups): group h holds the
+        // subset rows h, h + Ht, h + 2Ht, ... Groups h < Ht-1 publish a partial
+        // tile in slot slot0 + h; group Ht-1 (the owner) adds the partials in
+        // group order and updates the tile. Owners only wait on items that never
+        // wait (non-owner items come first in every block's sequence).
         float *best = sd.best;
-        const int H = sd.groups;
-        const int n_items = sd.n_tiles * H, n_nonowner = sd.n_tiles * (H - 1);
         const int C = g.C;
         const float beta = sd.beta;
-        for (int item = lb; item < n_items; item += grp.nblocks) {
-            const bool owner = item >= n_nonowner;
-            const int t = owner ? item - n_nonowner : item % sd.n_tiles;
-            const int h = owner ? H - 1 : item / sd.n_tiles;
+        auto process_item = [&](int t, int h, int Ht, int slot0) -> bool {
+            const bool owner = h == Ht - 1;
             const int i_lo = (t / sd.tiles_x) * kTile, j_lo = (t % sd.tiles_x) * kTile;
-            const int wpos = splat_views(g, sd.views, s, h, g.Vs, H, nullptr, i_lo, j_lo, sh.acc, sh.stage, sh.win,
+            const int wpos = splat_views(g, sd.views, s, h, g.Vs, Ht, nullptr, i_lo, j_lo, sh.acc, sh.stage, sh.win,
                                          [e4, C](int k, int) { return StageE4{e4 + (size_t)k * C}; });
             float part_val[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) part_val[u] = tile_sum(sh.acc, threadIdx.x + u * kThreads, kWarps, wpos);
 
             if (!owner) {
-                const size_t slot = (size_t)t * (H - 1) + h;
+                const size_t slot = (size_t)slot0 + h;
                 float *dst = sd.tile_part + slot * (kTile * kTile);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) __stcg(dst + threadIdx.x + u * kThreads, part_val[u]);
@@ -326,7 +321,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                     st_release(sd.tile_flag + slot, stamp);
                 }
                 __syncthreads(); // sh.acc is zeroed by the next item
-                continue;
+                return true;
             }
             if (!lam_done) {
                 if (!obtain_lambda()) return false;
@@ -337,19 +332,18 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
 
             if (threadIdx.x == 0) {
                 bool ok = true;
-                for (int hh = 0; hh < H - 1 && ok; ++hh)
-                    ok = wait_flag(sd.tile_flag + (size_t)t * (H - 1) + hh, stamp, err, a.timeout_ns,
-                                   a.spin_cap);
+                for (int hh = 0; hh < Ht - 1 && ok; ++hh)
+                    ok = wait_flag(sd.tile_flag + (size_t)slot0 + hh, stamp, err, a.timeout_ns, a.spin_cap);
                 sh.ok = ok;
             }
             __syncthreads();
             if (!sh.ok) return false;
 
-            // partial tiles of groups 0..H-2, added in group order (four pixels' loads
+            // partial tiles of groups 0..Ht-2, added in group order (four pixels' loads
             // in flight per group)
             float gsum[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int hh = 0; hh < H - 1; ++hh) {
-                const float *src = sd.tile_part + ((size_t)t * (H - 1) + hh) * (kTile * kTile) + threadIdx.x;
+            for (int hh = 0; hh < Ht - 1; ++hh) {
+                const float *src = sd.tile_part + ((size_t)slot0 + hh) * (kTile * kTile) + threadIdx.x;
                 float v[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) v[u] = __ldcg(src + u * kThreads);
@@ -393,6 +387,22 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 if (i < g.n && j < g.n) pnxtT[(size_t)j * g.n + i] = to_storage<TS>(tile[ii * kAccStride + jj]);
             }
             __syncthreads(); // tile (sh.acc[0]) is zeroed by the next item
+            return true;
+        };
+        if (sd.bitems) {
+            // balanced plan: at most one item per block, from the table
+            const int4 e = __ldg(sd.bitems + lb);
+            if (e.x >= 0 && !process_item(e.x, e.y, e.z, e.w)) return false;
+        } else {
+            // uniform plan: every tile in H groups; items lb, lb + nblocks, ...
+            const int H = sd.groups;
+            const int n_items = sd.n_tiles * H, n_nonowner = sd.n_tiles * (H - 1);
+            for (int item = lb; item < n_items; item += grp.nblocks) {
+                const bool owner = item >= n_nonowner;
+                const int t = owner ? item - n_nonowner : item % sd.n_tiles;
+                const int h = owner ? H - 1 : item / sd.n_tiles;
+                if (!process_item(t, h, H, t * (H - 1))) return false;
+            }
         }
         if (!lam_done && !obtain_lambda()) return false; // blocks without an owner item keep the same state
         if (!group_sync(grp.count, err, bk, grp.nblocks, 0u, a.timeout_ns, a.spin_cap)) return false;
@@ -509,6 +519,44 @@ int slice_groups(const mvct_plan_s *P, int nblocks, int override_h)
     if (override_h > 0) return std::max(1, std::min(override_h, P->groups_cap));
     if (P->tuned_groups > 0) return std::max(1, std::min(P->tuned_groups, P->groups_cap));
     return std::max(1, std::min(P->groups, nblocks / P->n_tiles));
+}
+
+bool balanced_items(int n_tiles, int Vs, int groups_cap, int grid, int num_sms, std::vector<int4> &items,
+                    int &idle_block)
+{
+    if (num_sms < 2 || grid % num_sms != 0) return false;
+    const int r = grid / num_sms, cap = std::min(groups_cap, Vs);
+    if (r < 2 || cap < 2) return false;
+    const int full_items = (r - 1) * num_sms; // rounds 0 .. r-2: two groups of a tile each
+    if (full_items % 2) return false;
+    const int full_tiles = full_items / 2, rest = n_tiles - full_tiles;
+    const int small = num_sms - 1; // round r-1 but its last block: the other tiles, split further
+    if (rest < 1 || small < 2 * rest || small > cap * rest) return false;
+    std::vector<int4> out(grid, make_int4(-1, 0, 0, 0));
+    int slot = 0;
+    for (int t = 0; t < full_tiles; ++t) {
+        out[2 * t] = make_int4(t, 0, 2, slot);
+        out[2 * t + 1] = make_int4(t, 1, 2, slot);
+        slot += 1;
+    }
+    int b = full_items;
+    for (int j = 0; j < rest; ++j) {
+        const int t = full_tiles + j, ct = small / rest + (j < small % rest ? 1 : 0);
+        for (int h = 0; h < ct; ++h) out[b++] = make_int4(t, h, ct, slot);
+        slot += ct - 1;
+    }
+    // every tile once in each of its groups, slots within the partial-tile buffers
+    std::vector<int> seen(n_tiles, 0);
+    for (const int4 &e : out)
+        if (e.x >= 0) seen[e.x] += 1 << e.y;
+    for (int t = 0; t < n_tiles; ++t) {
+        const int ht = t < full_tiles ? 2 : small / rest + (t - full_tiles < small % rest ? 1 : 0);
+        if (seen[t] != (1 << ht) - 1) return false;
+    }
+    if (b != grid - 1 || slot > n_tiles * (groups_cap - 1)) return false;
+    items.swap(out);
+    idle_block = grid - 1;
+    return true;
 }
 
 } // namespace mvct
@@ -689,6 +737,10 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     sd.tiles_x = P->tiles_x;
     sd.n_tiles = P->n_tiles;
     sd.groups = slice_groups(P, P->grid);
+    // the balanced plan for the default shape, else every tile in sd.groups groups
+    const bool table = P->bitems && P->tuned_groups == 0 && P->grid == P->recon_grid;
+    sd.bitems = table ? P->bitems : nullptr;
+    sd.reducer = table ? P->bitems_reducer : (P->n_tiles * sd.groups < P->grid ? P->n_tiles * sd.groups : -1);
     sd.beta = (float)beta;
     GroupDesc gd{0, P->grid, 0, 1, P->d_count, P->partials};
 
@@ -1022,6 +1074,8 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
         sd.tiles_x = P->tiles_x;
         sd.n_tiles = P->n_tiles;
         sd.groups = slice_groups(P, b->group_blocks[i], b->groups_override);
+        sd.bitems = nullptr;
+        sd.reducer = P->n_tiles * sd.groups < b->group_blocks[i] ? P->n_tiles * sd.groups : -1;
         sd.beta = (float)betas[i];
     }
     cudaError_t e = cudaMemcpy(b->d_slices, h.data(), sizeof(SliceDesc) * b->count, cudaMemcpyHostToDevice);
@@ -1208,17 +1262,19 @@ extern "C" int mvct_plan_tune(mvct_plan P, const float *d_sino, const float *d_w
         *ms = best;
         return MVCT_OK;
     };
+    // the default rule first (groups 0: the balanced plan where there is one)
+    const int default_report = P->bitems ? 0 : default_groups;
     double default_ms = 0.0;
-    int rc = probe(P->recon_grid, default_groups, &default_ms);
-    int best_grid = P->recon_grid, best_groups = default_groups;
+    int rc = probe(P->recon_grid, default_report, &default_ms);
+    int best_grid = P->recon_grid, best_groups = default_report;
     double best_ms = default_ms;
-    report_add(report, default_groups, P->recon_grid, default_ms);
+    report_add(report, default_report, P->recon_grid, default_ms);
     const int max_bps = P->recon_grid / std::max(1, P->num_sms);
     const int hs[] = {1, 2, 3, 4, 6, 8};
     for (int bps = max_bps; rc == MVCT_OK && bps >= std::max(1, max_bps - 2); --bps) {
         const int grid = std::min(P->recon_grid, bps * P->num_sms);
         for (int h : hs) {
-            if (h > P->groups_cap || (grid == P->recon_grid && h == default_groups)) continue;
+            if (h > P->groups_cap || (grid == P->recon_grid && h == default_report)) continue;
             double ms = 0.0;
             rc = probe(grid, h, &ms);
             if (rc) break;

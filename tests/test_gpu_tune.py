@@ -51,11 +51,13 @@ def test_every_shape_matches_oracle(mvct, groups, bps):
 
 
 def test_full_size_shapes_agree(mvct):
-    """512^2, 800 x 738: 8 groups on 2 blocks per SM (about 7 items per block)
-    against the default shape, 6 sub-iterations."""
+    """512^2, 800 x 738: 8 groups on 2 blocks per SM (about 7 items per block),
+    one group per tile on 3 blocks per SM, and two groups per tile on every
+    block against the default shape (the balanced plan of items), 6
+    sub-iterations."""
     c = ph.make_case("full", 100)
     out = {}
-    for shape in [(0, 0), (8, 2 * sms()), (1, 3 * sms())]:
+    for shape in [(0, 0), (8, 2 * sms()), (1, 3 * sms()), (2, 0)]:
         with mvct.Plan(c.geom, c.n_subsets) as plan:
             plan.set_shape(*shape)
             img, res = plan.recon(cuda(c.p), cuda(c.w), c.beta, 6)
