@@ -327,6 +327,21 @@ int mvct_plan_tune(mvct_plan plan, const float *d_sino, const float *d_weights, 
  * groups. A groups value > 0 always splits every tile into that many groups. */
 int mvct_plan_set_shape(mvct_plan plan, int32_t groups, int32_t grid_blocks);
 
+/* The balanced plan of phase B that a one-slice launch of the default shape
+ * uses (see mvct_plan_set_shape), as plain host arithmetic: n_tiles 32x32
+ * tiles, views_per_subset views per subset, groups_cap = min(8, views per
+ * subset) partial-tile buffers per tile, grid blocks on num_sms SMs (block b
+ * assumed on SM b mod num_sms). Group h of a tile split into H groups holds the
+ * subset's views h, h + H, h + 2H, ... On success writes 4 * grid int32 to
+ * items (per block: tile, view group, view groups of that tile, first
+ * partial-tile slot of that tile; tile -1 for a block without an item) and the
+ * item-less block that reduces Phi_n to *idle_block, and returns 1; returns 0,
+ * writing nothing, when the sizes do not allow the plan (the launch then splits
+ * every tile into the same number of groups); MVCT_EINVAL for a NULL pointer or
+ * a size < 1. Makes no CUDA call. */
+int mvct_phase_b_plan(int32_t n_tiles, int32_t views_per_subset, int32_t groups_cap, int32_t grid,
+                      int32_t num_sms, int32_t *items, int32_t *idle_block);
+
 /* Tune a bound batch: the view groups per tile of every slice (the default
  * rule, or 1, 2, 3, 4, 6, 8) with runs of min(n_iter_probe, max_iter)
  * sub-iterations on the bound data; the bound images are saved before and

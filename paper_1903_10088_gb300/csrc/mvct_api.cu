@@ -335,3 +335,22 @@ extern "C" int mvct_objective(mvct_plan P, const float *d_img, const float *d_si
     CK(launch_final_sum(P->partials, P->reduce_grid, 0.5, P->partials2, P->reduce_grid, beta, d_out, st));
     return MVCT_OK;
 }
+
+extern "C" int mvct_phase_b_plan(int32_t n_tiles, int32_t views_per_subset, int32_t groups_cap, int32_t grid,
+                                 int32_t num_sms, int32_t *items, int32_t *idle_block)
+{
+    if (!items || !idle_block) return mvct_fail(MVCT_EINVAL, "mvct_phase_b_plan: null output");
+    if (n_tiles < 1 || views_per_subset < 1 || groups_cap < 1 || grid < 1 || num_sms < 1)
+        return mvct_fail(MVCT_EINVAL, "mvct_phase_b_plan: sizes must be >= 1");
+    std::vector<int4> plan;
+    int idle = -1;
+    if (!balanced_items(n_tiles, views_per_subset, groups_cap, grid, num_sms, plan, idle)) return 0;
+    for (int b = 0; b < grid; ++b) {
+        items[4 * b + 0] = plan[b].x;
+        items[4 * b + 1] = plan[b].y;
+        items[4 * b + 2] = plan[b].z;
+        items[4 * b + 3] = plan[b].w;
+    }
+    *idle_block = idle;
+    return 1;
+}

@@ -121,7 +121,7 @@ EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvc
            "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
            "mvct_batch_run", "mvct_batch_stats", "mvct_fbp", "mvct_cnn_param_count", "mvct_cnn_create",
            "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step", "mvct_plan_tune", "mvct_batch_tune",
-           "mvct_plan_set_shape"]
+           "mvct_plan_set_shape", "mvct_phase_b_plan"]
 
 
 def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
@@ -163,6 +163,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     lib.mvct_plan_tune.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(TuneReport), vp]
     lib.mvct_batch_tune.argtypes = [vp, i32, ctypes.POINTER(TuneReport), vp]
     lib.mvct_plan_set_shape.argtypes = [vp, i32, i32]
+    lib.mvct_phase_b_plan.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     lib.mvct_last_error.restype = ctypes.c_char_p
     lib.mvct_last_error.argtypes = []
     return lib
@@ -203,6 +204,20 @@ def geometry(g) -> Geometry:
 
 
 STORAGE = {"f32": 0, "bf16": 1, "f16": 2}   # mvct_recon_opts.storage (MVCT_STORAGE_*)
+
+
+def phase_b_plan(n_tiles: int, views_per_subset: int, groups_cap: int, grid: int, num_sms: int):
+    """``mvct_phase_b_plan``: the balanced phase-B plan of the default one-slice
+    launch shape, as an int32 array [grid][4] (tile, view group, view groups of
+    the tile, first partial slot; tile -1: no item) and the reducer block, or
+    None when the sizes do not allow it. Host arithmetic only (no GPU needed)."""
+    items = np.zeros((grid, 4), dtype=np.int32)
+    idle = ctypes.c_int32(-1)
+    rc = lib().mvct_phase_b_plan(n_tiles, views_per_subset, groups_cap, grid, num_sms,
+                                 items.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(idle))
+    if rc < 0:
+        raise MvctError(rc, lib().mvct_last_error().decode())
+    return (items, idle.value) if rc == 1 else None
 
 
 def spread_order(S: int) -> List[int]:
