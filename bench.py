@@ -96,9 +96,9 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic():
-    """DRAM bytes per k_recon launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def ncu_record():
+    """The committed ncu figures of one k_recon launch of the plain workload, if
+    they were taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "k_recon_traffic.json")
     if not os.path.exists(path):
         return None
@@ -106,7 +106,29 @@ def ncu_traffic():
         d = json.load(f)
     if d.get("kernel_source_sha256_16") != kernel_source_hash():
         return None
-    return d.get("dram_bytes_per_launch_full_workload")
+    return d
+
+
+def ncu_traffic():
+    """DRAM bytes per k_recon launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    d = ncu_record()
+    return d.get("dram_bytes_per_launch_full_workload") if d else None
+
+
+def issue_roofline(warp_instructions, seconds, n_sms, sm_mhz):
+    """Instruction-issue view of a kernel: warp instructions per second against
+    the issue rate of the GPU, one warp instruction per cycle on each of the 4
+    schedulers of every SM at the sampled SM clock. The loop kernel's taps are
+    L1/L2 hits, so issue (not HBM) is what bounds it."""
+    if not warp_instructions or not seconds or not n_sms or not sm_mhz:
+        return None
+    peak = 4.0 * n_sms * sm_mhz * 1e6
+    achieved = warp_instructions / seconds
+    return {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "G warp-instructions/s",
+            "frac": achieved / peak,
+            "warp_instructions_per_launch": warp_instructions,
+            "peak_source": f"4 issue slots x {n_sms} SMs x {sm_mhz:.0f} MHz (median sampled SM clock)",
+            "instructions_source": "smsp__inst_executed.sum of the committed ncu capture of this launch"}
 
 
 class ClockSampler:
@@ -420,6 +442,10 @@ def run_ours(args):
         "grid_blocks": res.grid_blocks,
         "warm_start_batched": warm,
     }
+    rec = ncu_record()
+    line["issue_roofline"] = issue_roofline(rec.get("warp_instructions_per_launch") if rec else None, loop_s,
+                                            torch.cuda.get_device_properties(dev).multi_processor_count,
+                                            line["clocks"].get("sm_mhz") or line["clocks"].get("sm_max_mhz"))
     if rank == 0:
         print(json.dumps(line))
     plan.close()
