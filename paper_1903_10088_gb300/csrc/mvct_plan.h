@@ -198,7 +198,8 @@ int slice_groups(const mvct_plan_s *P, int nblocks, int override_h = 0);
 // (block b assumed on SM b mod num_sms): every SM gets r - 1 items of half a
 // tile's views (r = grid / num_sms blocks per SM) and one small item of a tile
 // split into 2..groups_cap groups; one block stays without an item. False (and
-// nothing written) when the sizes do not allow it.
+// nothing written) when the sizes do not allow it. The placement is only an
+// assumption (the hardware decides it); the results do not depend on it.
 bool balanced_items(int n_tiles, int Vs, int groups_cap, int grid, int num_sms, std::vector<int4> &items,
                     int &idle_block);
 
