@@ -375,7 +375,8 @@ class Plan:
 
 def _plan_tune(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter_probe: int = 40, stream=None) -> dict:
     """``mvct_plan_tune``: time the loop's launch-shape candidates on (p, w) and
-    keep the fastest for this plan; returns the report as a dict."""
+    keep the fastest for this plan; returns the report as a dict (groups 0 = the
+    default rule, i.e. the balanced phase-B plan where the sizes allow it)."""
     R = self.V * self.C
     rep = TuneReport()
     _check(lib().mvct_plan_tune(self._h, _dev_f32(p, R, "p"), _dev_f32(w, R, "w"), beta, n_iter_probe,
@@ -384,7 +385,10 @@ def _plan_tune(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter_probe
 
 
 def _plan_set_shape(self, groups: int = 0, grid_blocks: int = 0) -> None:
-    """``mvct_plan_set_shape``: fix the loop's launch shape (0 = default)."""
+    """``mvct_plan_set_shape``: fix the loop's launch shape. groups = view groups
+    per tile (0: the default rule, the balanced plan where the sizes allow it;
+    > 0: every tile split into that many groups), grid_blocks = blocks of the
+    launch (0: every co-resident block)."""
     _check(lib().mvct_plan_set_shape(self._h, groups, grid_blocks))
 
 
