@@ -192,6 +192,23 @@ def test_tv_gradient_finite_differences():
     assert rel(grad, fd) < 1e-6
 
 
+def test_objective_is_half_weighted_residual_plus_beta_tv(A8):
+    """Psi = 1/2 sum w (A mu - p)^2 + beta TV_eps(mu) (Eq. 1-2 with R1, R3, R12):
+    the data term through the brute-force matrix, the TV term on a vertical step
+    whose TV has the closed form of test_tv_vertical_step_closed_form."""
+    n, eps, beta, h = G8.n, 1e-6, 3e-3, 0.013
+    img = np.full((n, n), 0.05)
+    img[:, 3:] += h
+    rng = np.random.default_rng(12)
+    p = A8 @ img.ravel() + rng.normal(0, 0.02, A8.shape[0])
+    w = rng.uniform(0.2, 1.0, A8.shape[0])
+    data = 0.5 * float(np.sum(w * (A8 @ img.ravel() - p) ** 2))
+    tv = n * math.sqrt(h * h + eps) + (n * n - n) * math.sqrt(eps)
+    got = oracle.objective(G8, img, p.reshape(G8.n_views, G8.n_channels), w.reshape(G8.n_views, G8.n_channels),
+                           beta, eps)
+    assert abs(got - (data + beta * tv)) <= 1e-11 * (data + beta * tv)
+
+
 # --------------------------------- set-up -----------------------------------
 def test_setup_diagonal_and_mask(A8):
     rng = np.random.default_rng(7)
