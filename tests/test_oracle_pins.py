@@ -264,6 +264,21 @@ def test_lambda_rule_and_best_iterate_follow_eq4_eq5():
     assert r["best_n"] == S - 1 + int(np.argmin(passes))
 
 
+def test_lambda_replay_reproduces_the_adaptive_run():
+    """Replaying an adaptive run's own lambda sequence (the mode the GPU parity
+    tests use to separate arithmetic from a flipped Eq. 4-5 decision) gives the
+    same iterates bit for bit; another schedule gives other iterates and is
+    taken verbatim."""
+    c = ph.make_case("small", 2)
+    n_iter = 12
+    r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, n_iter)
+    rr = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, n_iter, lambda_schedule=r["lam"])
+    assert np.array_equal(rr["image"], r["image"]) and np.array_equal(rr["lam"], r["lam"])
+    r2 = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, n_iter, lambda_schedule=np.full(n_iter, 0.005))
+    assert np.all(r2["lam"] == 0.005)
+    assert rel(r2["image"], r["image"]) > 1e-3
+
+
 def test_first_step_is_preconditioned_gradient_step(A8):
     """One sub-iteration with S subsets equals mu0 - tau D (S A_s^T W_s (A_s mu0 - p_s)
     + beta grad TV), clamped at 0, with A_s taken from the brute-force matrix."""
