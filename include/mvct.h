@@ -150,7 +150,13 @@ void mvct_plan_destroy(mvct_plan plan);
 int mvct_forward(mvct_plan plan, const float *d_img, float *d_sino, int32_t subset, void *stream);
 
 /* Estimation (Sec. 4.4): d_img = A_s^T d_sino, the matched adjoint of
- * mvct_forward, gathered per pixel without atomics (deterministic).
+ * mvct_forward (the projector's own Joseph weights, so <A x, y> = <x, A^T y>
+ * up to FP32 rounding). Computed ray-driven, not pixel-driven: each 32x32 pixel
+ * tile is owned by one block, whose warps walk the rays of the tile's channel
+ * window through it and add their weighted values into warp-private
+ * shared-memory copies of the tile, which are then summed in a fixed order (per
+ * tile, view groups are merged in group order). No global atomics and no
+ * floating-point race, so results are bit-identical from run to run.
  * Overwrites all n*n pixels. */
 int mvct_back(mvct_plan plan, const float *d_sino, float *d_img, int32_t subset, void *stream);
 

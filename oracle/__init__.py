@@ -56,11 +56,15 @@ class OracleParams(ctypes.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable C99, no arch-specific flags)."""
+    """Compile the oracle with gcc (portable C99, no arch-specific flags), with
+    OpenMP if the compiler has it (used only when set_threads() asks for it)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        r = subprocess.run(base + ["-fopenmp"], capture_output=True)
+        if r.returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,11 +84,19 @@ def _load():
             lib.oracle_objective.restype = ctypes.c_double
             lib.oracle_setup.argtypes = [G, dp, ctypes.c_double, ctypes.c_double, dp,
                                          ctypes.POINTER(ctypes.c_ubyte)]
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             lib.oracle_recon.argtypes = [G, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_int,
                                          ctypes.POINTER(OracleParams), dp, dp, dp, dp, dp,
                                          ctypes.POINTER(ctypes.c_int), dp]
             _lib = lib
     return _lib
+
+
+def set_threads(threads: int) -> int:
+    """Threads for the reprojection (rays) and the transpose (views); results are
+    bit-identical for any count. Returns the count in effect (1 without OpenMP)."""
+    return _load().oracle_set_threads(int(threads))
 
 
 def _geom(g) -> OracleGeometry:

@@ -36,8 +36,13 @@ def fan_filter(C: int, a: float) -> np.ndarray:
     return g
 
 
-def fbp(geom, sino) -> np.ndarray:
-    """FBP image [n][n] (1/cm) from log projections [V][C] of `geom`."""
+def fbp(geom, sino, threads: int = 1) -> np.ndarray:
+    """FBP image [n][n] (1/cm) from log projections [V][C] of `geom`.
+
+    threads > 1 (a timed CPU baseline over the host cores) backprojects
+    contiguous runs of views in worker threads, each into its own image (views in
+    order), and adds the run images in run order: the same sum as threads = 1 up
+    to the grouping of the additions (pinned to 1e-12 relative)."""
     n, V, C = geom.n, geom.n_views, geom.n_channels
     a = geom.fan / C
     D = geom.sad_cm
@@ -52,24 +57,39 @@ def fbp(geom, sino) -> np.ndarray:
     delta = geom.fov_cm / n
     cen = (np.arange(n) - (n - 1) / 2.0) * delta
     X, Y = np.meshgrid(cen, cen)            # X[i, j] = x_j, Y[i, j] = y_i
-    img = np.zeros((n, n))
     dbeta = 2.0 * math.pi / V
     c_mid = (C - 1) / 2.0 - geom.channel_offset
-    for v in range(V):
-        b = geom.view0_rad + 2.0 * math.pi * v / V
-        sx, sy = D * math.cos(b), D * math.sin(b)
-        ex, ey = -math.cos(b), -math.sin(b)            # central ray direction
-        px, py = X - sx, Y - sy
-        dot = px * ex + py * ey
-        crs = ex * py - ey * px
-        gp = np.arctan2(crs, dot)                       # angle of the pixel's ray
-        L2 = px * px + py * py
-        u = gp / a + c_mid                              # fractional channel index
-        k0 = np.floor(u).astype(np.int64)
-        f = u - k0
-        val = np.zeros_like(u)
-        for kk, wt in ((k0, 1.0 - f), (k0 + 1, f)):
-            ok = (kk >= 0) & (kk < C)
-            val[ok] += wt[ok] * q[v, kk[ok]]
-        img += dbeta * val / L2
+
+    def back_views(v0, v1):
+        img = np.zeros((n, n))
+        for v in range(v0, v1):
+            b = geom.view0_rad + 2.0 * math.pi * v / V
+            sx, sy = D * math.cos(b), D * math.sin(b)
+            ex, ey = -math.cos(b), -math.sin(b)            # central ray direction
+            px, py = X - sx, Y - sy
+            dot = px * ex + py * ey
+            crs = ex * py - ey * px
+            gp = np.arctan2(crs, dot)                       # angle of the pixel's ray
+            L2 = px * px + py * py
+            u = gp / a + c_mid                              # fractional channel index
+            k0 = np.floor(u).astype(np.int64)
+            f = u - k0
+            val = np.zeros_like(u)
+            for kk, wt in ((k0, 1.0 - f), (k0 + 1, f)):
+                ok = (kk >= 0) & (kk < C)
+                val[ok] += wt[ok] * q[v, kk[ok]]
+            img += dbeta * val / L2
+        return img
+
+    threads = max(1, min(int(threads), V))
+    if threads == 1:
+        return back_views(0, V)
+    import concurrent.futures as cf
+
+    cuts = [V * t // threads for t in range(threads + 1)]
+    with cf.ThreadPoolExecutor(threads) as ex:
+        parts = list(ex.map(back_views, cuts[:-1], cuts[1:]))
+    img = parts[0]
+    for part in parts[1:]:
+        img = img + part
     return img

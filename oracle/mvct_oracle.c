@@ -5,8 +5,13 @@
  * product path. It shares no code with the CUDA library.
  *
  * Plain, slow, obviously correct: every operator is written out the way the
- * method defines it, in double precision, single-threaded, with no blocking,
- * fusion or reordering.
+ * method defines it, in double precision, with no blocking, fusion or
+ * reordering. It runs on one thread unless oracle_set_threads() asks for more
+ * (a timed CPU baseline over all host cores); then only two loops are shared
+ * out, each without changing a single rounding: the reprojection's rays (each
+ * ray's sum is its own) and the transpose's views (every view still scatters
+ * into its own private image, and the view images are added to the result in
+ * view order, pixel by pixel). Results are bit-identical for any thread count.
  *
  *   Problem (Sec. 2, Eq. 1-2): maximise ln P(mu|y) = L(mu) + alpha R(mu) subject
  *     to mu > 0; L from Poisson statistics, R the total variation.
@@ -28,6 +33,25 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads used by oracle_forward / oracle_back (1 unless set). */
+static int g_threads = 1;
+
+/* Set the thread count (clamped to >= 1); returns the count in effect, which is
+ * 1 when the library was built without OpenMP. */
+int oracle_set_threads(int threads)
+{
+#ifdef _OPENMP
+    g_threads = threads < 1 ? 1 : threads;
+#else
+    (void)threads;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
 
 typedef struct {
     int32_t n;              /* image n x n, row-major, row i = y, column j = x */
@@ -181,11 +205,12 @@ static int check(const oracle_geometry *g, int subset, int n_subsets)
 int oracle_forward(const oracle_geometry *g, const double *img, int subset, int n_subsets, double *sino)
 {
     if (check(g, subset, n_subsets)) return -1;
-    int rows = subset_rows(g, subset, n_subsets);
-    for (int k = 0; k < rows; ++k) {
-        int v = subset_view(subset, n_subsets, k);
-        for (int c = 0; c < g->n_channels; ++c)
-            sino[(size_t)k * g->n_channels + c] = joseph_ray(g, img, v, c);
+    int rows = subset_rows(g, subset, n_subsets), C = g->n_channels;
+    long long n_rays = (long long)rows * C;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
+    for (long long i = 0; i < n_rays; ++i) {
+        int k = (int)(i / C), c = (int)(i % C);
+        sino[i] = joseph_ray(g, img, subset_view(subset, n_subsets, k), c);
     }
     return 0;
 }
@@ -197,16 +222,26 @@ int oracle_back(const oracle_geometry *g, const double *sino, int subset, int n_
 {
     if (check(g, subset, n_subsets)) return -1;
     size_t nn = (size_t)g->n * g->n;
-    double *view_img = (double *)malloc(nn * sizeof(double));
+    int T = g_threads;                       /* views scattered at a time */
+    double *view_img = (double *)malloc((size_t)T * nn * sizeof(double));
     if (!view_img) return -2;
     memset(img, 0, nn * sizeof(double));
     int rows = subset_rows(g, subset, n_subsets);
-    for (int k = 0; k < rows; ++k) {
-        int v = subset_view(subset, n_subsets, k);
-        memset(view_img, 0, nn * sizeof(double));
-        for (int c = 0; c < g->n_channels; ++c)
-            joseph_ray_transpose(g, sino[(size_t)k * g->n_channels + c], v, c, view_img);
-        for (size_t r = 0; r < nn; ++r) img[r] += view_img[r];
+    for (int k0 = 0; k0 < rows; k0 += T) {
+        int kn = rows - k0 < T ? rows - k0 : T;
+        /* views k0 .. k0+kn-1, each into its own image */
+#pragma omp parallel for schedule(static, 1) num_threads(T) if (T > 1)
+        for (int t = 0; t < kn; ++t) {
+            int v = subset_view(subset, n_subsets, k0 + t);
+            double *vi = view_img + (size_t)t * nn;
+            memset(vi, 0, nn * sizeof(double));
+            for (int c = 0; c < g->n_channels; ++c)
+                joseph_ray_transpose(g, sino[(size_t)(k0 + t) * g->n_channels + c], v, c, vi);
+        }
+        /* and added to the result in view order */
+#pragma omp parallel for schedule(static) num_threads(T) if (T > 1)
+        for (long long r = 0; r < (long long)nn; ++r)
+            for (int t = 0; t < kn; ++t) img[r] += view_img[(size_t)t * nn + r];
     }
     free(view_img);
     return 0;

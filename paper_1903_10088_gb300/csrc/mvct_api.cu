@@ -309,7 +309,8 @@ extern "C" int mvct_tv_grad(mvct_plan P, const float *d_img, double eps, float *
     int rc = mvct_check_ptrs(P->device, stream, "mvct_tv_grad", {d_img, d_grad});
     if (rc == MVCT_OK && d_tv_or_null) rc = mvct_check_ptrs(P->device, stream, "mvct_tv_grad", {d_tv_or_null});
     if (rc) return rc;
-    if (!(eps > 0) || !std::isfinite(eps)) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: eps must be > 0");
+    if (!mvct_eps_ok(eps))
+        return mvct_fail(MVCT_EINVAL, "mvct_tv_grad: eps must be > 0 and a normal float (>= FLT_MIN)");
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
     CK(launch_tv(P, d_img, (float)eps, d_grad, P->partials, st));
@@ -324,7 +325,7 @@ extern "C" int mvct_objective(mvct_plan P, const float *d_img, const float *d_si
     if (!P) return mvct_fail(MVCT_EINVAL, "mvct_objective: null plan");
     int rc = mvct_check_ptrs(P->device, stream, "mvct_objective", {d_img, d_sino, d_weights, d_out});
     if (rc) return rc;
-    if (!(eps > 0) || !std::isfinite(eps) || !std::isfinite(beta))
+    if (!mvct_eps_ok(eps) || !std::isfinite(beta))
         return mvct_fail(MVCT_EINVAL, "mvct_objective: invalid beta/eps");
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;

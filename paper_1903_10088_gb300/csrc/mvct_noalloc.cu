@@ -60,7 +60,8 @@ extern "C" int mvct_tv_grad_noalloc(const float *d_img, int32_t n, double eps, f
     if (n < 1 || n > MVCT_MAX_N)
         return mvct_fail(MVCT_EINVAL, "mvct_tv_grad_noalloc: n = %d outside 1..%d (the static scratch "
                          "serves images up to %d x %d)", n, MVCT_MAX_N, MVCT_MAX_N, MVCT_MAX_N);
-    if (!(eps > 0) || !std::isfinite(eps)) return mvct_fail(MVCT_EINVAL, "mvct_tv_grad_noalloc: eps must be > 0");
+    if (!mvct_eps_ok(eps))
+        return mvct_fail(MVCT_EINVAL, "mvct_tv_grad_noalloc: eps must be > 0 and a normal float (>= FLT_MIN)");
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return mvct_fail(MVCT_ECUDA, "mvct_tv_grad_noalloc: %s", cudaGetErrorString(e));

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cfloat>
+#include <cmath>
 #include <vector>
 
 #include "mvct.h"
@@ -207,6 +209,14 @@ bool balanced_items(int n_tiles, int Vs, int groups_cap, int grid, int num_sms, 
 
 // FBP tables of a plan (mvct_fbp.cu).
 int mvct_fbp_tables(mvct_plan_s *P);
+
+// The TV smoothing eps is applied in FP32 (inside the square root of every
+// pixel term): it must be finite, > 0 and stay a normal float when rounded,
+// otherwise a flat region gives 0 * rsqrt(0) = NaN gradients.
+inline bool mvct_eps_ok(double eps)
+{
+    return eps > 0 && std::isfinite(eps) && (float)eps >= FLT_MIN && std::isfinite((float)eps);
+}
 
 // Error reporting shared by the translation units (mvct_api.cu).
 int mvct_fail(int code, const char *fmt, ...);

@@ -632,7 +632,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     mvct_recon_opts o;
     if (opts_in) o = *opts_in;
     else mvct_recon_opts_init(&o);
-    if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
+    if (!mvct_eps_ok(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
         !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
         (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
         return mvct_fail(MVCT_EINVAL, "mvct_recon: invalid options");
@@ -852,6 +852,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
 struct mvct_batch_s {
     int device = 0, count = 0, grid = 0, ngroups = 0, max_iter = 0;
     int groups_override = 0;            // > 0: view groups per tile of every slice (autotuner)
+    bool param_kernel = false;          // launch k_recon_pb (descriptors in the kernel parameters)
     std::vector<mvct_plan_s *> plans;   // user order
     std::vector<int> pos;               // user slice -> position in the descriptor array
     std::vector<int> group_blocks;      // blocks of the group of each user slice
@@ -1001,6 +1002,17 @@ extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_bat
         free_batch(b);
         return mvct_fail(MVCT_ECUDA, "mvct_batch_create: %s", cudaGetErrorString(e));
     }
+    // The parameter-space kernel serves batches whose descriptors fit its
+    // parameters, if the whole grid of it can be co-resident; the choice is made
+    // here so that a launch (possibly captured into a graph) never has to retry.
+    if (count <= kParamSlices && b->ngroups <= kParamSlices) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_recon_pb<float>, kThreads, 0) != cudaSuccess) {
+            cudaGetLastError();
+            nb = 0;
+        }
+        b->param_kernel = (long long)nb * plans[0]->num_sms >= G;
+    }
     for (auto *p : b->plans) p->in_batch = true;
     *out = b;
     return MVCT_OK;
@@ -1027,7 +1039,7 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
     if (o.lambda_schedule || o.state || o.d_best_out || o.subset_order)
         return mvct_fail(MVCT_EINVAL,
                          "mvct_batch_bind: lambda_schedule, state, d_best_out and subset_order are one-slice options");
-    if (!(o.tv_eps > 0) || !std::isfinite(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
+    if (!mvct_eps_ok(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
         !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
         (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
         return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: invalid options");
@@ -1135,7 +1147,7 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
         a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
         cudaError_t le;
-        if (b->count <= kParamSlices && b->ngroups <= kParamSlices) {
+        if (b->param_kernel) {
             // descriptors in the kernel parameters (copied at launch, captured by graphs)
             std::unique_ptr<BatchParams> bp(new BatchParams());
             std::memcpy(bp->sl, b->h_slices.data(), sizeof(SliceDesc) * b->count);
@@ -1143,12 +1155,6 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
             void *args[] = {&a, bp.get()};
             le = cudaLaunchCooperativeKernel((const void *)k_recon_pb<float>, dim3(b->grid), dim3(kThreads), args, 0,
                                              st);
-            if (le != cudaSuccess) { // e.g. fewer co-resident blocks: the descriptor-array kernel
-                cudaGetLastError();
-                void *args1[] = {&a};
-                le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads), args1, 0,
-                                                 st);
-            }
         } else {
             void *args[] = {&a};
             le = cudaLaunchCooperativeKernel((const void *)k_recon<true>, dim3(b->grid), dim3(kThreads), args, 0, st);

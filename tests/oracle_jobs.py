@@ -36,3 +36,27 @@ def full_case_recon_checkpoints(seed: int, beta: float, checkpoints):
         r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, beta, n)
         out[n] = (r["image"].astype(np.float64), r["lam"])
     return out
+
+
+def fbp_start(c):
+    """The plain form's start image: the oracle's FBP of the case, rounded to FP32
+    (the same host array is handed to the oracle and to the GPU)."""
+    from oracle import fbp as F
+
+    return F.fbp(c.geom, c.p.astype(np.float64)).astype(np.float32)
+
+
+def full_case_recon_from(seed: int, beta: float, n_iter: int, start):
+    """Oracle reconstruction of the seeded full-size case from a given start image."""
+    c = ph.make_case("full", seed, beta=beta, n_iter=n_iter)
+    r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, beta, n_iter, init=np.asarray(start, dtype=np.float64))
+    return r["image"].astype(np.float64), r["phi"], r["lam"]
+
+
+def case_recon_from(seed: int, geom, beta: float, n_iter: int, start, lambda0: float):
+    """Oracle reconstruction of a seeded full-kind case on `geom` from a start image
+    with the given lambda0."""
+    c = ph.make_case("full", seed, geom=geom, beta=beta, n_iter=n_iter)
+    r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, beta, n_iter, init=np.asarray(start, dtype=np.float64),
+                     lambda0=lambda0)
+    return r["image"].astype(np.float64), r["phi"], r["lam"]

@@ -84,3 +84,22 @@ def test_null_plan_calls_fail_cleanly(libmvct):
     assert libmvct.mvct_tv_grad(None, None, 1e-6, None, None, None) == -1
     assert libmvct.mvct_recon(None, None, None, 0.0, 1, None, None, None, None) == -1
     libmvct.mvct_plan_destroy(None)
+
+
+@pytest.mark.parametrize("eps", [0.0, -1e-6, 1e-50, 1e-40, float("inf"), float("nan"), 1e300])
+def test_tv_eps_that_is_not_a_normal_float_is_rejected(libmvct, eps):
+    """eps enters every pixel term in FP32: a value that rounds to 0 or to a
+    subnormal float (or overflows) would give 0 * rsqrt(0) = NaN gradients on
+    flat regions, so it is refused before any CUDA call (the dummy pointers are
+    never touched)."""
+    bogus = ctypes.c_void_p(0x1000)
+    assert libmvct.mvct_tv_grad_noalloc(bogus, 8, eps, bogus, None, None) == -1
+    assert b"normal float" in libmvct.mvct_last_error()
+
+
+def test_smallest_normal_float_eps_passes_the_check(libmvct):
+    """FLT_MIN itself is accepted by the eps check: the call gets past it and fails
+    only later, for want of a device, with another message."""
+    bogus = ctypes.c_void_p(0x1000)
+    libmvct.mvct_tv_grad_noalloc(bogus, 8, 1.1754944e-38, bogus, None, None)
+    assert b"normal float" not in libmvct.mvct_last_error()

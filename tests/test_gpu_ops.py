@@ -168,6 +168,13 @@ def test_full_size_projector_sampled(mvct):
     refb = oracle.back(g, y[7::20].astype(np.float64), 7, 20)
     assert rel(bs, refb) < RTOL_PROJ
     assert np.all(np.isfinite(b))
+    # the all-view backprojection path: by linearity, a full sinogram that is zero
+    # except on the rows of subset 7 backprojects to the oracle's subset-7 image
+    y7 = np.zeros_like(y)
+    y7[7::20] = y[7::20]
+    with mvct.Plan(g, 20) as plan:
+        b7 = host(plan.back(cuda(y7)))
+    assert rel(b7, refb) < RTOL_PROJ
 
 
 def test_invalid_subset_rejected(mvct):

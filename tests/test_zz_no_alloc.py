@@ -1,13 +1,15 @@
 """The allocation-free TV entry point (mvct_tv_grad_noalloc) agrees with the
-plan-based mvct_tv_grad.
+plan-based mvct_tv_grad and with the FP64 oracle.
 
 mvct_tv_grad_noalloc exists for callers that may not allocate device memory
 (applications whose GPU memory is handed out by their own allocator, or
 latency-critical paths where cudaMalloc, which can synchronise the device, is
 off limits). It keeps its partial sums in a static device array shared by all
 calls, so this test calls it twice in a row, with different images and sizes,
-and checks each result against the existing entry point within the tolerances
-the operator tests use (gradient 1e-5 relative L2, FP64-reduced value 1e-6).
+and checks each result against the existing entry point and against the FP64
+oracle's TV within the tolerances the operator tests use (gradient 1e-5
+relative L2, FP64-reduced value 1e-6), so a fault shared by both CUDA entry
+points cannot pass unseen.
 
 This file is collected last so that a run stopping at the first failure has
 run every other test first; it also passes on its own in a fresh process.
@@ -17,6 +19,8 @@ import ctypes
 import numpy as np
 import pytest
 import torch
+
+import oracle
 
 from paper_1903_10088_gb300 import phantom as ph
 
@@ -55,6 +59,9 @@ def test_noalloc_tv_matches_plan_entry_point_twice(mvct):
         torch.cuda.synchronize()
         assert rel(grad.cpu().numpy(), ref_grad.cpu().numpy()) < 1e-5
         assert abs(float(tv.cpu()) - float(ref_tv.cpu())) <= 1e-6 * float(ref_tv.cpu())
+        o_tv, o_grad = oracle.tv(img.double().cpu().numpy(), eps)
+        assert rel(grad.cpu().numpy(), o_grad) < 1e-5
+        assert abs(float(tv.cpu()) - o_tv) <= 1e-6 * o_tv
 
 
 def test_noalloc_rejects_sizes_beyond_the_maximum(mvct):
