@@ -222,6 +222,54 @@ def barrier():
 # --------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # --------------------------------------------------------------------------
+def cpu_info() -> dict:
+    """Host cores and CPU model (lscpu, else /proc/cpuinfo, else the platform)."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                model = line.split(":", 1)[1].strip()
+                break
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def time_oracle_slice(case, threads: int):
+    """One whole slice of the plain form by the oracle, unextrapolated: its FBP
+    over all views (threaded view runs), then set-up + every sub-iteration from
+    that start, with `threads` threads (the oracle's results do not depend on the
+    count). Returns (seconds, sample description)."""
+    import oracle
+    from oracle import fbp as ofbp
+
+    oracle.build()
+    used = oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        start = ofbp.fbp(case.geom, case.p, threads=threads)
+        t_fbp = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.recon(case.geom, case.n_subsets, case.p, case.w, case.beta, case.n_iter, init=start)
+        t_loop = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    sample = (f"FP64 oracle, {used} threads (OpenMP over rays and views, bit-identical to 1 thread), one "
+              f"whole slice, not extrapolated: FBP of all {case.geom.n_views} views {t_fbp:.2f} s, set-up + "
+              f"{case.n_iter} sub-iterations {t_loop:.2f} s")
+    return t_fbp + t_loop, sample, used
+
+
 def time_oracle(case, sub_iters: int):
     """Oracle FBP start + set-up + `sub_iters` sub-iterations; returns (seconds
     per slice at the full sub-iteration count, sample description). The FBP is
@@ -252,26 +300,34 @@ def time_oracle(case, sub_iters: int):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, one whole slice of the
+    plain form per step (FBP of all views + set-up + 500 sub-iterations), with
+    as many threads as the host has cores. Warm-up steps run a short sample."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    import oracle
+
     case = ph.make_case("full", SEED0)
-    steps = []
-    sample = ""
+    threads = args.ref_threads or os.cpu_count() or 1
+    short = ph.make_case("full", SEED0, n_iter=2)
     for _ in range(args.warmup):
-        time_oracle(case, 2)
+        time_oracle_slice(short, threads)
+    steps, sample, used = [], "", 1
+    wall0 = time.perf_counter()
     for _ in range(args.steps):
-        t_slice, sample = time_oracle(case, args.ref_sub_iters)
+        t_slice, sample, used = time_oracle_slice(case, threads)
         steps.append(t_slice)
-    t = float(np.mean(steps))
+    wall = time.perf_counter() - wall0
+    t = float(np.sum(steps)) / max(1, args.steps)
     value = 1.0 / t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(WORKLOAD, l2="n/a (CPU)"),
-        "cpu_baseline": {"value": value, "unit": "slices/s", "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": dict({"value": value, "unit": "slices/s", "cores": used, "kind": "oracle",
+                              "sample": sample, "timed_wall_s": wall}, **cpu_info()),
         "e2e": {"value": value, "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -371,7 +427,9 @@ def run_ours(args):
                 "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "kernel": "k_recon (persistent OS-TV loop)",
                 "algorithmic_bytes": "4 B x (Joseph reprojection taps + matched-backprojection residual reads) "
-                                     f"= {tap_bytes:.4g} B per launch",
+                                     f"= {tap_bytes:.4g} B per launch; a tap-byte rate: the taps are served "
+                                     "from L1/L2 (the image stays resident), so this is not DRAM traffic "
+                                     "(see dram_roofline and issue_roofline)",
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
     gray = 2.0 * taps_per_launch / loop_s / 1e9
 
@@ -403,10 +461,38 @@ def run_ours(args):
         nb = op_bytes["all_views" if "all" in k else "one_subset"]
         operators[k] = {"ms": t * 1e3, "achieved_gbs": nb / t / 1e9, "frac": nb / t / 1e9 / peaks["hbm_gbs"]}
 
+    # the TV-weight sweep of the workload (beta = 1e-3 is the timed step above)
+    sweep = []
+    for beta in (1e-4, 1e-3, 1e-2):
+        def bstep():
+            plan.fbp(p, out=img)
+            return plan.recon(p, w, beta, case.n_iter, img=img, init_from_input=True)
+        bstep()
+        ms = []
+        for k in range(3):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bstep()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        psi = float(plan.objective(img, p, w, beta, case.tv_eps).cpu())
+        sweep.append({"beta": beta, "slices_per_s": 1e3 / float(np.mean(ms)), "ms_per_slice": float(np.mean(ms)),
+                      "psi_500": psi})
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_slice, sample = time_oracle(case, args.ref_sub_iters)
-        cpu = {"value": 1.0 / t_slice, "unit": "slices/s", "cores": 1, "kind": "oracle", "sample": sample}
+        t_all, sample_all, used = time_oracle_slice(case, args.ref_threads or os.cpu_count() or 1)
+        t_one, sample_one = time_oracle(case, args.ref_sub_iters)
+        cpu = dict({"value": 1.0 / t_all, "unit": "slices/s", "cores": used, "kind": "oracle",
+                    "sample": sample_all,
+                    "single_thread": {"value": 1.0 / t_one, "unit": "slices/s", "cores": 1, "sample": sample_one}},
+                   **cpu_info())
+
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(args, dev, ws, steps=2, warmup=1)
 
     warm = None
     if not args.no_warm:
@@ -440,9 +526,18 @@ def run_ours(args):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk.summary(),
         "grid_blocks": res.grid_blocks,
+        "beta_sweep": sweep,
+        "batched_uneven": batched,
         "warm_start_batched": warm,
     }
     rec = ncu_record()
+    if traffic:
+        # what the loop kernel really moves through HBM (ncu DRAM bytes of one launch,
+        # taken on this kernel source) over the same launch time
+        line["dram_roofline"] = {"bound": "hbm", "achieved": traffic / loop_s / 1e9, "peak": peaks["hbm_gbs"],
+                                 "unit": "GB/s", "frac": traffic / loop_s / 1e9 / peaks["hbm_gbs"],
+                                 "bytes_source": "dram__bytes_read.sum + dram__bytes_write.sum of the committed "
+                                                 "ncu capture of this launch"}
     line["issue_roofline"] = issue_roofline(rec.get("warp_instructions_per_launch") if rec else None, loop_s,
                                             torch.cuda.get_device_properties(dev).multi_processor_count,
                                             line["clocks"].get("sm_mhz") or line["clocks"].get("sm_max_mhz"))
@@ -581,9 +676,116 @@ def batch_cases(seed0=1000, groups=ph.BATCH_GROUPS, workers=8):
         return list(ex.map(_make_batch_case, jobs))
 
 
+def batched_leg(args, dev, ws, steps, warmup):
+    """The batched uneven stack (96 slices of three geometries, 500 sub-iterations
+    each, one persistent launch per step, autotuned view groups, replayed as one
+    CUDA graph). Returns its JSON object; per-slice parity of the batch kernel at
+    these sizes is the job of tests/test_gpu_bench_parity.py."""
+    import torch
+
+    from paper_1903_10088_gb300 import mvct
+
+    _, rank, local = dist_env()
+    cases = batch_cases(seed0=1000 + 96 * rank, workers=min(16, os.cpu_count() or 1))
+    n_iter = cases[0].n_iter
+    plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
+    p = [torch.from_numpy(c.p).to(dev) for c in cases]
+    w = [torch.from_numpy(c.w).to(dev) for c in cases]
+    imgs = [torch.zeros((c.geom.n, c.geom.n), device=dev) for c in cases]
+    batch = mvct.Batch(plans)
+    batch.bind(p, w, [c.beta for c in cases], imgs, n_iter)
+    tune = batch.tune(40)                             # view groups per tile (untimed; images restored)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    batch.run(n_iter, stream=s)                       # first call outside capture
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            batch.run(n_iter, stream=s)
+    torch.cuda.synchronize(dev)
+    for _ in range(warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    batch.stats(0, n_iter)                            # raises if the runs failed
+    cur = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local, "_batched") as clk:
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(cur)
+            graph.replay()
+            ev[k][1].record(cur)
+        torch.cuda.synchronize(dev)
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_max = max_over_ranks(float(np.sum(step_ms)), dev)
+    n_slices = len(cases) * ws * steps
+    value = n_slices / (t_max / 1e3)
+
+    # end to end: every slice's p and w from pinned host memory, every image back
+    hp = [torch.from_numpy(c.p).pin_memory() for c in cases]
+    hw = [torch.from_numpy(c.w).pin_memory() for c in cases]
+    hi = [torch.empty(im.shape, dtype=torch.float32).pin_memory() for im in imgs]
+    e2e_ms = []
+    for k in range(max(1, steps)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        for a, b in zip(p, hp):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(w, hw):
+            a.copy_(b, non_blocking=True)
+        graph.replay()
+        for a, b in zip(hi, imgs):
+            a.copy_(b, non_blocking=True)
+        e1.record(cur)
+        torch.cuda.synchronize(dev)
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_t = max_over_ranks(float(np.sum(e2e_ms)), dev)
+
+    work = [c.geom.n_views / c.n_subsets * c.geom.n_channels * c.geom.n for c in cases]
+    w512 = 800 / 20 * 738 * 512
+    equiv_slices = sum(work) / w512
+    taps = [tap_counts(c.geom, c.n_subsets) for c in cases]
+    tap_total = sum(float(sum(t[n % c.n_subsets] for n in range(n_iter))) for t, c in zip(taps, cases))
+    peaks, peak_kind = load_peaks()
+    t_step = float(np.mean(step_ms)) / 1e3
+    achieved = 2 * 4 * tap_total / t_step / 1e9
+    out = {
+        "value": value, "unit": "slices/s", "ms_per_step": t_max / steps, "steps": steps, "warmup": warmup,
+        "config": dict(BATCH_WORKLOAD, l2="flushed between timed steps (512 MiB write)",
+                       launch_shape={"view_groups_per_tile": tune["groups"] or "default rule",
+                                     "autotuned_ms_per_iter": tune["ms_per_iter"],
+                                     "default_ms_per_iter": tune["default_ms_per_iter"]}),
+        "slices_512_equivalent_per_s": equiv_slices * ws * steps / (t_max / 1e3),
+        "us_per_512_equivalent_slice_sub_iteration": t_step * 1e6 / (equiv_slices * n_iter),
+        "gray_per_s": 2.0 * tap_total / t_step / 1e9,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "kernel": "batch set-up + k_recon_pb (one graph replay)",
+                     "algorithmic_bytes": "4 B x (reprojection taps + backprojection residual reads), "
+                                          "served from L1/L2",
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": len(cases) * ws * len(e2e_ms) / (e2e_t / 1e3), "unit": "slices/s",
+                "h2d_bytes_per_step": int(sum(t.numel() * 4 for t in hp + hw)),
+                "d2h_bytes_per_step": int(sum(t.numel() * 4 for t in hi))},
+        "parity": "tests/test_gpu_bench_parity.py: the batch kernel at 512^2, 384^2 and 256^2 against the "
+                  "oracle (40 sub-iterations) and one-slice runs (500)",
+        "clocks": clk.summary(),
+        "gpu_launches_per_step": 2 + 3 * len(cases),
+    }
+    batch.close()
+    for pl in plans:
+        pl.close()
+    return out
+
+
 def run_batched(args):
-    """Batched workload: all slices of the stack reconstructed per step."""
-    cases = batch_cases()
+    """Batched workload on its own: all slices of the stack reconstructed per step."""
     import torch
     import torch.distributed as dist
 
@@ -595,71 +797,14 @@ def run_batched(args):
     from paper_1903_10088_gb300 import mvct
 
     mvct.lib()
-    n_iter = cases[0].n_iter
-    plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
-    p = [torch.from_numpy(c.p).to(dev) for c in cases]
-    w = [torch.from_numpy(c.w).to(dev) for c in cases]
-    imgs = [torch.zeros((c.geom.n, c.geom.n), device=dev) for c in cases]
-    batch = mvct.Batch(plans)
-    batch.bind(p, w, [c.beta for c in cases], imgs, n_iter)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
-    s = torch.cuda.Stream()
-    s.wait_stream(torch.cuda.current_stream())
-    batch.run(n_iter, stream=s)                       # first call outside capture
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.stream(s):
-        with torch.cuda.graph(graph, stream=s):
-            batch.run(n_iter, stream=s)
-    torch.cuda.synchronize()
-    for _ in range(args.warmup):
-        graph.replay()
-    torch.cuda.synchronize()
-    batch.stats(0, n_iter)                            # raises if the runs failed
-    cur = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local, "_batched") as clk:
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            ev[k][0].record(cur)
-            graph.replay()
-            ev[k][1].record(cur)
-        torch.cuda.synchronize()
-    barrier()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_max = max_over_ranks(float(np.sum(step_ms)), dev)
-    n_slices = len(cases) * ws * args.steps
-    value = n_slices / (t_max / 1e3)
-    work = [c.geom.n_views / c.n_subsets * c.geom.n_channels * c.geom.n for c in cases]
-    w512 = 800 / 20 * 738 * 512
-    equiv = sum(work) / w512 * ws * args.steps / (t_max / 1e3)
-    taps = [tap_counts(c.geom, c.n_subsets) for c in cases]
-    tap_total = sum(float(sum(t[n % c.n_subsets] for n in range(n_iter))) for t, c in zip(taps, cases))
-    peaks, peak_kind = load_peaks()
-    achieved = 2 * 4 * tap_total / (np.mean(step_ms) / 1e3) / 1e9
-    line = {
-        "metric": "slices/s of the batched uneven stack at 500 OS-TV iters (plain start)", "value": value,
-        "unit": "slices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": dict(BATCH_WORKLOAD, l2="flushed between timed steps (512 MiB write)",
-                       parallelism=f"replicas x{ws}, one stack per GPU per step"),
-        "slices_512_equivalent_per_s": equiv,
-        "gray_per_s": 2.0 * tap_total / (np.mean(step_ms) / 1e3) / 1e9,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "kernel": "k_recon<batch> + set-up (whole graph)",
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
-        "clocks": clk.summary(),
-        "gpu_launches": (2 + 3 * len(cases)) * args.steps,
-    }
+    leg = batched_leg(args, dev, ws, args.steps, args.warmup)
+    line = dict({"metric": "slices/s of the batched uneven stack at 500 OS-TV iters (plain start)",
+                 "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                 "dtype": "f32", "data": "synthetic", "gpu_launches": leg["gpu_launches_per_step"] * args.steps},
+                **leg)
+    line["config"] = dict(line["config"], parallelism=f"replicas x{ws}, one stack per GPU per step")
     if rank == 0:
         print(json.dumps(line))
-    batch.close()
-    for pl in plans:
-        pl.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
@@ -716,6 +861,9 @@ def main(argv=None):
                     help="oracle sub-iterations timed per reference sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-started batched form")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven stack")
+    ap.add_argument("--ref-threads", type=int, default=0,
+                    help="oracle threads for the whole-slice CPU timing (0: every host core)")
     ap.add_argument("--workload", choices=["plain", "batched", "subsets"], default="plain")
     args = ap.parse_args(argv)
     if args.impl == "reference":

@@ -75,6 +75,7 @@ typedef struct mvct_recon_state {
     double best_pass;     /* smallest pass sum so far (+inf if none) */
     int64_t best_n;       /* its sub-iteration (-1 if none) */
     double phi_ring[MVCT_MAX_SUBSETS]; /* last S square differences, slot n mod S */
+    double pass_prev;     /* MVCT_LAMBDA_PASS: the last complete pass sum that was recorded */
 } mvct_recon_state;
 
 /* Options of mvct_recon. Fill with mvct_recon_opts_init() first. */
@@ -83,7 +84,8 @@ typedef struct mvct_recon_opts {
     double dlambda_up;    /* Eq. 4 increment when the square difference fell (1e-4) */
     double dlambda_down;  /* Eq. 5 decrement when it rose (2e-4) */
     double lambda_min;    /* floor of lambda (1e-4) */
-    double kappa;         /* step tau = kappa * lambda on the preconditioned gradient (100) */
+    double kappa;         /* step tau = kappa * lambda on the preconditioned gradient (50: lambda0 = 0.01 is
+                             half the separable-surrogate step) */
     double tv_eps;        /* TV smoothing inside the square root (1e-6) */
     double mu0;           /* homogeneous initial image in 1/cm, Sec. 3.3.2 (0.05) */
     int32_t init_from_input;       /* 1: start from d_img_inout instead of mu0 */
@@ -98,7 +100,31 @@ typedef struct mvct_recon_opts {
                                       (sub-iteration n uses subset subset_order[n mod S]); NULL: the
                                       paper's equal-interval subsets in order 0, 1, ..., S-1 (Sec. 3.4).
                                       mvct_recon only; MVCT_EINVAL if not a permutation */
+    int32_t lambda_rule;           /* which square differences Eq. 4-5 compare: MVCT_LAMBDA_* below
+                                      (default MVCT_LAMBDA_PASS_SLIDING) */
+    double *psi_record;            /* host, n_iter/S + 1 doubles, or NULL: the convergence record of
+                                      Sec. 4.2 -- psi_record[k] = Psi (mvct_objective over all views) of
+                                      the iterate after k*S sub-iterations of this call, k = 0 ..
+                                      n_iter/S (k = 0: the start image). The loop then runs one pass
+                                      per launch, resumed bit for bit. mvct_recon only */
 } mvct_recon_opts;
+
+/* Readings of Eq. 4-5 under ordered subsets. Sec. 3.3.2 raises lambda when "the
+ * square of difference between a reprojection and a projection" decreases and
+ * lowers it when it increases; with subsets each sub-iteration n only has the
+ * square difference Phi_n of its own subset's rays. The rules say which values
+ * are compared (lambda unchanged on a tie and where no comparison is made):
+ *   SUBSET        Phi_n with Phi_{n-1}, n >= 1 (consecutive sub-iterations, i.e.
+ *                 different subsets);
+ *   PASS          once per pass: at n = kS, k >= 2, the sum over the last complete
+ *                 pass Phi_{n-S} + ... + Phi_{n-1} with the pass before it;
+ *   PASS_SLIDING  every sub-iteration n >= S: the pass sum P_n = Phi_{n-S+1} + ... +
+ *                 Phi_n with P_{n-1}, i.e. Phi_n with Phi_{n-S}, the same subset one
+ *                 pass earlier (the whole-sinogram square difference, refreshed one
+ *                 subset at a time). */
+#define MVCT_LAMBDA_SUBSET 0
+#define MVCT_LAMBDA_PASS 1
+#define MVCT_LAMBDA_PASS_SLIDING 2
 
 /* Storage precision of mvct_recon. F32: every buffer FP32. BF16 / F16: the copies
  * of the iterate that the reprojection reads (the image and its transpose) and
@@ -133,7 +159,8 @@ typedef struct mvct_recon_stats {
     int32_t block_threads;
 } mvct_recon_stats;
 
-/* Default options (the paper's constants: lambda0 0.01, +1e-4, -2e-4; mu0 0.05). */
+/* Default options (the paper's constants: lambda0 0.01, +1e-4, -2e-4; mu0 0.05; kappa 50 and
+ * MVCT_LAMBDA_PASS_SLIDING, the readings under which the paper's convergence claims hold). */
 void mvct_recon_opts_init(mvct_recon_opts *opts);
 
 /* Build a plan for geometry *g with n_subsets ordered subsets (Sec. 3.4:

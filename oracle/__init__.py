@@ -52,7 +52,12 @@ class OracleParams(ctypes.Structure):
         ("init_from_input", ctypes.c_int32),
         ("data_term", ctypes.c_int32),
         ("subset_order", ctypes.POINTER(ctypes.c_int32)),
+        ("lambda_rule", ctypes.c_int32),
     ]
+
+
+# which square difference drives Eq. 4-5 (see oracle_recon in mvct_oracle.c)
+LAMBDA_RULES = {"subset": 0, "pass": 1, "pass_sliding": 2}
 
 
 def build(force: bool = False) -> str:
@@ -171,14 +176,16 @@ def setup(g, w, beta: float, eps: float):
     return D, M.astype(bool)
 
 
-DEFAULTS = dict(lambda0=0.01, dlambda_up=1e-4, dlambda_down=2e-4, lambda_min=1e-4, kappa=100.0,
-                tv_eps=1e-6, mu0=0.05, data_term=0)
+DEFAULTS = dict(lambda0=0.01, dlambda_up=1e-4, dlambda_down=2e-4, lambda_min=1e-4, kappa=50.0,
+                tv_eps=1e-6, mu0=0.05, data_term=0, lambda_rule="pass_sliding")
 
 
 def recon(g, n_subsets: int, p, w, beta: float, n_iter: int, init=None, lambda_schedule=None,
           want_best: bool = False, subset_order=None, **params):
     """Run the OS-TV loop; returns dict(image, phi, lam, best_n, best_pass, best_image).
-    subset_order: a permutation of 0..S-1 visited cyclically (default 0, 1, ..., S-1)."""
+    subset_order: a permutation of 0..S-1 visited cyclically (default 0, 1, ..., S-1).
+    lambda_rule: "subset", "pass" or "pass_sliding" (which square differences Eq. 4-5
+    compare; see oracle_recon in mvct_oracle.c)."""
     prm = dict(DEFAULTS)
     prm.update(params)
     order = None
@@ -188,7 +195,8 @@ def recon(g, n_subsets: int, p, w, beta: float, n_iter: int, init=None, lambda_s
             raise ValueError("subset_order must be a permutation of 0..S-1")
     op = OracleParams(prm["lambda0"], prm["dlambda_up"], prm["dlambda_down"], prm["lambda_min"],
                       prm["kappa"], prm["tv_eps"], prm["mu0"], 1 if init is not None else 0, prm["data_term"],
-                      order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if order is not None else None)
+                      order.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)) if order is not None else None,
+                      LAMBDA_RULES[prm["lambda_rule"]])
     img = np.zeros((g.n, g.n)) if init is None else _f64(init).reshape(g.n, g.n).copy()
     phi = np.zeros(max(n_iter, 1))
     lam = np.zeros(max(n_iter, 1))

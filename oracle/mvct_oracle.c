@@ -76,7 +76,17 @@ typedef struct {
     int32_t init_from_input;/* 1: start from the caller's image instead of mu0 */
     int32_t data_term;      /* 0: weighted least squares on log projections; 1: Poisson log-likelihood */
     const int32_t *subset_order; /* S entries, a permutation of 0..S-1 visited cyclically; NULL: 0, 1, ..., S-1 */
+    int32_t lambda_rule;    /* which square difference drives Eq. 4-5 (see oracle_recon) */
 } oracle_recon_params;
+
+/* Readings of "the objective function being the square of difference between a
+ * reprojection and a projection" (Sec. 3.3.2) under ordered subsets. */
+enum {
+    LAMBDA_SUBSET = 0,       /* Phi_n against Phi_{n-1}: consecutive sub-iterations (different subsets) */
+    LAMBDA_PASS = 1,         /* once per pass: the sum over the last complete pass against the pass before */
+    LAMBDA_PASS_SLIDING = 2  /* every sub-iteration: the pass sum P_n = Phi_{n-S+1} + ... + Phi_n against
+                                P_{n-1}, i.e. Phi_n against Phi_{n-S} (the same subset one pass earlier) */
+};
 
 static const double PI = 3.14159265358979323846;
 
@@ -305,7 +315,7 @@ static double tv_curvature_bound(double eps) { return 8.0 / sqrt(eps); }
 /* Set-up of the loop. Support mask M_r = [(A^T 1)_r > 0] over all views (pixels
  * no ray reaches are held at 0), and the separable-quadratic-surrogate diagonal
  *   D_r = 1 / ( (A^T (w .* (A 1)))_r + beta * 8/sqrt(eps) )   on M, else 0,
- * which majorises the Hessian of Psi so that a unit step (kappa*lambda0 = 1)
+ * which majorises the Hessian of Psi so that a unit step (tau = kappa*lambda = 1)
  * decreases Psi for a full-gradient step. */
 int oracle_setup(const oracle_geometry *g, const double *w, double beta, double eps,
                  double *D, unsigned char *M)
@@ -341,8 +351,14 @@ int oracle_setup(const oracle_geometry *g, const double *w, double beta, double 
  *   e   = w_s - exp(-q)               (data_term 1: gradient of the negative Poisson
  *                                      log-likelihood sum(y q + I0 exp(-q)) divided by
  *                                      I0, with counts y = I0 w)
- *   lambda_n = lambda0 at n = 0; otherwise lambda_{n-1} + up if Phi_n < Phi_{n-1},
- *              - down if Phi_n > Phi_{n-1}, unchanged on a tie; floored at lambda_min.
+ *   lambda_n = lambda0 at n = 0; otherwise lambda_{n-1} + up if the square
+ *              difference fell, - down if it rose, unchanged on a tie or when the
+ *              rule makes no comparison at n; floored at lambda_min. Which square
+ *              differences are compared (lambda_rule):
+ *                SUBSET        Phi_n with Phi_{n-1} (n >= 1);
+ *                PASS          at n = kS, k >= 2: Phi_{n-S} + ... + Phi_{n-1} with
+ *                              Phi_{n-2S} + ... + Phi_{n-S-1} (the last two passes);
+ *                PASS_SLIDING  Phi_n with Phi_{n-S} (n >= S): the pass sum P_n with P_{n-1}.
  *              (lambda_schedule, if given, replaces the rule.)
  *   g   = A_s^T e                        (estimation)
  *   mu' = max(0, mu - kappa lambda_n D .* (S g + beta grad TV_eps(mu))), 0 off M
@@ -391,11 +407,25 @@ int oracle_recon(const oracle_geometry *g, int n_subsets, const double *p, const
             }
         }
         phis[it] = phi;
+        /* the two square differences Eq. 4-5 compare at this sub-iteration, if any */
+        int decide = 0;
+        double now = 0.0, before = 0.0;
+        if (prm->lambda_rule == LAMBDA_PASS_SLIDING) {
+            if (it >= S) { decide = 1; now = phi; before = phis[it - S]; }
+        } else if (prm->lambda_rule == LAMBDA_PASS) {
+            if (it >= 2 * S && it % S == 0) {
+                decide = 1;
+                for (int k = it - S; k < it; ++k) now += phis[k];
+                for (int k = it - 2 * S; k < it - S; ++k) before += phis[k];
+            }
+        } else if (it > 0) {
+            decide = 1; now = phi; before = phi_prev;
+        }
         if (lambda_schedule) {
             lambda = lambda_schedule[it];
-        } else if (it > 0) {
-            if (phi < phi_prev) lambda += prm->dlambda_up;
-            else if (phi > phi_prev) lambda -= prm->dlambda_down;
+        } else if (decide) {
+            if (now < before) lambda += prm->dlambda_up;
+            else if (now > before) lambda -= prm->dlambda_down;
             if (lambda < prm->lambda_min) lambda = prm->lambda_min;
         }
         phi_prev = phi;

@@ -53,10 +53,12 @@ struct SliceDesc {
 // Phi_n by the group's reducer block (PhiPub, the second line).
 constexpr int kGroupSyncWords = 64;
 struct PhiPub {
-    unsigned int stamp;       // barrier count after which phi and pass are valid
+    unsigned int stamp;       // barrier count after which the values below are valid
     unsigned int pad;
     double phi;               // Phi_n
     double pass;              // Phi_{n-S+1} + ... + Phi_n
+    double phi_old;           // Phi_{n-S} (0 for n < S)
+    double pass_last;         // Phi_{n-S} + ... + Phi_{n-1}, the last complete pass (n >= S)
 };
 static_assert(sizeof(PhiPub) <= 128, "PhiPub fits one line");
 inline __host__ __device__ PhiPub *phi_pub(unsigned int *count)
@@ -85,6 +87,7 @@ struct LoopArgs {
     unsigned long long timeout_ns, spin_cap;
     int debug_unreachable;
     int poisson;              // 1: Poisson data term, e = w - exp(-q)
+    int lambda_rule;          // MVCT_LAMBDA_*: which square differences Eq. 4-5 compare
 };
 
 // Batches of up to kParamSlices slices pass their descriptors in the kernel

@@ -58,8 +58,9 @@ __device__ __forceinline__ bool wait_flag(const unsigned int *flag, unsigned int
 // Shared state of one block of the loop kernel.
 struct LoopShared {
     double warp[kWarps];
-    double lambda, phi_prev, best_pass;
+    double lambda, phi_prev, best_pass, pass_prev;
     double phi_n, pass_n;          // Phi_n and the pass sum of the current sub-iteration
+    double phi_old, pass_last;     // Phi_{n-S} and the last complete pass sum (n >= S)
     long long best_n;
     float tau;
     int best_flag, ok;
@@ -88,6 +89,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         sh.phi_prev = st->phi_prev;
         sh.best_pass = st->best_pass;
         sh.best_n = st->best_n;
+        sh.pass_prev = st->pass_prev;
     }
     __syncthreads();
     const long long n0 = st->n_done;
@@ -185,8 +187,10 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         // the same fixed order, so every block derives the same lambda_n and
         // best-iterate decision.
         const int slot_n = (int)(n % g.S);
-        const bool full = n >= g.S - 1;
+        const bool full = n >= g.S - 1, seen_pass = n >= g.S;
         const int reducer = sd.reducer;
+        // the block that stores Phi_n into the ring (after the closing barrier)
+        const int ring_writer = reducer >= 0 ? reducer : 0;
         PhiPub *pub = phi_pub(grp.count);
         const unsigned int pub_stamp = bk;
         // all threads: Phi_n and the pass sum Phi_{n-S+1} + ... + Phi_n into sh
@@ -210,17 +214,24 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 double phi = 0.0;
                 for (int k = 0; k < kWarps; ++k) phi += sh.warp[k];
                 // the last S values of Phi live in the slice's state (global
-                // memory): the reducer (block 0 without one) writes slot n mod S;
-                // the other slots were written in earlier sub-iterations, ordered
-                // by the group barriers
-                if (lane == 0 && lb == (reducer >= 0 ? reducer : 0)) st->phi_ring[slot_n] = phi;
-                double pass = 0.0;
+                // memory), slot k mod S for sub-iteration k. Slot n mod S still
+                // holds Phi_{n-S}: the ring writer stores Phi_n only after this
+                // sub-iteration's closing barrier, so no block reads a slot while
+                // it is written; the barriers order the earlier stores.
+                double pass = 0.0, pass_last = 0.0;
                 if (full)
-                    for (int k = lane; k < g.S; k += 32) pass += (k == slot_n) ? phi : st->phi_ring[k];
+                    for (int k = lane; k < g.S; k += 32) {
+                        const double v = st->phi_ring[k];
+                        pass += (k == slot_n) ? phi : v;
+                        pass_last += v;
+                    }
                 pass = warp_sum(pass);
+                pass_last = warp_sum(pass_last);
                 if (lane == 0) {
                     sh.phi_n = phi;
                     sh.pass_n = pass;
+                    sh.phi_old = seen_pass ? st->phi_ring[slot_n] : 0.0;
+                    sh.pass_last = seen_pass ? pass_last : 0.0;
                 }
             }
             __syncthreads();
@@ -235,11 +246,30 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                 } else if (n == 0) {
                     lam = a.lambda0;
                 } else {
+                    // the two square differences this rule compares at n, if any
+                    bool decide = false;
+                    double now = 0.0, before = 0.0;
+                    if (a.lambda_rule == MVCT_LAMBDA_PASS_SLIDING) {
+                        decide = seen_pass;
+                        now = phi;
+                        before = sh.phi_old;
+                    } else if (a.lambda_rule == MVCT_LAMBDA_PASS) {
+                        decide = n >= 2 * (long long)g.S && slot_n == 0;
+                        now = sh.pass_last;
+                        before = sh.pass_prev;
+                    } else {
+                        decide = true;
+                        now = phi;
+                        before = sh.phi_prev;
+                    }
                     lam = sh.lambda;
-                    if (phi < sh.phi_prev) lam += a.dup;
-                    else if (phi > sh.phi_prev) lam -= a.ddown;
-                    if (lam < a.lmin) lam = a.lmin;
+                    if (decide) {
+                        if (now < before) lam += a.dup;
+                        else if (now > before) lam -= a.ddown;
+                        if (lam < a.lmin) lam = a.lmin;
+                    }
                 }
+                if (a.lambda_rule == MVCT_LAMBDA_PASS && seen_pass && slot_n == 0) sh.pass_prev = sh.pass_last;
                 sh.lambda = lam;
                 sh.phi_prev = phi;
                 int bf = 0;
@@ -268,6 +298,8 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
                     if (ok) {
                         sh.phi_n = __ldcg(&pub->phi);
                         sh.pass_n = __ldcg(&pub->pass);
+                        sh.phi_old = __ldcg(&pub->phi_old);
+                        sh.pass_last = __ldcg(&pub->pass_last);
                     }
                     sh.ok = ok;
                 }
@@ -282,6 +314,8 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             if (threadIdx.x == 0) {
                 pub->phi = sh.phi_n;
                 pub->pass = sh.pass_n;
+                pub->phi_old = sh.phi_old;
+                pub->pass_last = sh.pass_last;
                 st_release(&pub->stamp, pub_stamp);
             }
             apply_lambda();
@@ -407,6 +441,9 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
         if (!lam_done && !obtain_lambda()) return false; // blocks without an owner item keep the same state
         if (!group_sync(grp.count, err, bk, grp.nblocks, 0u, a.timeout_ns, a.spin_cap)) return false;
         ++bk;
+        // every block has read the ring of this sub-iteration: store Phi_n (the next
+        // barrier orders it before the next sub-iteration's reads)
+        if (lb == ring_writer && threadIdx.x == 0) st->phi_ring[slot_n] = sh.phi_n;
         if (timer) {
             const unsigned long long now = global_ns();
             t_b += now - t_mark;
@@ -421,6 +458,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             st->phi_prev = sh.phi_prev;
             st->best_pass = sh.best_pass;
             st->best_n = sh.best_n;
+            st->pass_prev = sh.pass_prev;
         }
     }
     __syncthreads(); // the next slice re-initialises the shared state
@@ -502,6 +540,7 @@ __global__ void k_state_init(mvct_recon_state *st, int count, double lambda0)
             st[b].phi_prev = 0.0;
             st[b].best_pass = INFINITY;
             st[b].best_n = -1;
+            st[b].pass_prev = 0.0;
         }
     }
 }
@@ -608,11 +647,75 @@ extern "C" void mvct_recon_opts_init(mvct_recon_opts *o)
     o->dlambda_up = 1e-4;
     o->dlambda_down = 2e-4;
     o->lambda_min = 1e-4;
-    o->kappa = 100.0;
+    o->kappa = 50.0;
+    o->lambda_rule = MVCT_LAMBDA_PASS_SLIDING;
     o->tv_eps = 1e-6;
     o->mu0 = 0.05;
     o->barrier_timeout_ms = 2000.0;
 }
+
+namespace {
+
+// mvct_recon with opts.psi_record: the loop one pass (S sub-iterations) per call,
+// resumed through a loop state (bit-identical to one run), with the objective
+// Psi of the iterate after every pass (and of the start image) on the host.
+int recon_with_psi(mvct_plan P, const float *d_sino, const float *d_weights, double beta, int32_t n_iter,
+                   const mvct_recon_opts &o, float *d_img, mvct_recon_stats *stats, void *stream)
+{
+    const int S = P->geo.S;
+    mvct_recon_state local;
+    std::memset(&local, 0, sizeof(local));
+    local.lambda = o.lambda0;
+    local.best_pass = INFINITY;
+    local.best_n = -1;
+    mvct_recon_opts oc = o;
+    oc.psi_record = nullptr;
+    oc.state = o.state ? o.state : &local;
+    auto psi_now = [&](double *out) -> int {
+        int rc = mvct_objective(P, d_img, d_sino, d_weights, beta, o.tv_eps, P->tv_sum, stream);
+        if (rc) return rc;
+        cudaError_t e = cudaMemcpyAsync(out, P->tv_sum, sizeof(double), cudaMemcpyDeviceToHost, (cudaStream_t)stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) return mvct_fail(MVCT_ECUDA, "mvct_recon: psi_record: %s", cudaGetErrorString(e));
+        return MVCT_OK;
+    };
+    mvct_recon_stats sc;
+    std::memset(&sc, 0, sizeof(sc));
+    int rc = mvct_recon(P, d_sino, d_weights, beta, 0, &oc, d_img, &sc, stream); // set-up: d_img = mu^(0)
+    if (rc) return rc;
+    if ((rc = psi_now(o.psi_record))) return rc;
+    oc.init_from_input = 1;
+    double loop_ms = 0, setup_ms = sc.setup_ms, fwd_ms = 0, back_ms = 0;
+    for (int done = 0; done < n_iter;) {
+        const int chunk = std::min(S, n_iter - done);
+        oc.lambda_schedule = o.lambda_schedule ? o.lambda_schedule + done : nullptr;
+        std::memset(&sc, 0, sizeof(sc));
+        if (stats) {
+            sc.phi = stats->phi ? stats->phi + done : nullptr;
+            sc.lambda = stats->lambda ? stats->lambda + done : nullptr;
+        }
+        if ((rc = mvct_recon(P, d_sino, d_weights, beta, chunk, &oc, d_img, &sc, stream))) return rc;
+        loop_ms += sc.loop_ms;
+        setup_ms += sc.setup_ms;
+        fwd_ms += sc.forward_ms;
+        back_ms += sc.back_ms;
+        done += chunk;
+        if (done % S == 0 && (rc = psi_now(o.psi_record + done / S))) return rc;
+    }
+    if (stats) {
+        stats->best_n = oc.state->best_n;
+        stats->best_pass = oc.state->best_pass;
+        stats->loop_ms = loop_ms;
+        stats->setup_ms = setup_ms;
+        stats->forward_ms = fwd_ms;
+        stats->back_ms = back_ms;
+        stats->grid_blocks = P->grid;
+        stats->block_threads = kThreads;
+    }
+    return MVCT_OK;
+}
+
+} // namespace
 
 extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weights, double beta,
                           int32_t n_iter, const mvct_recon_opts *opts_in, float *d_img_inout,
@@ -634,7 +737,9 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     else mvct_recon_opts_init(&o);
     if (!mvct_eps_ok(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
         !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
-        (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
+        (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON) ||
+        (o.lambda_rule != MVCT_LAMBDA_SUBSET && o.lambda_rule != MVCT_LAMBDA_PASS &&
+         o.lambda_rule != MVCT_LAMBDA_PASS_SLIDING))
         return mvct_fail(MVCT_EINVAL, "mvct_recon: invalid options");
     if (o.state && (o.state->n_done < 0 || (o.state->n_done > 0 && !o.init_from_input)))
         return mvct_fail(MVCT_EINVAL, "mvct_recon: resuming (state->n_done > 0) needs init_from_input = 1");
@@ -652,6 +757,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
     if (P->recon_grid <= 0) return mvct_fail(MVCT_ELAUNCH, "mvct_recon: loop kernel has no occupancy");
 
     if (P->in_batch) return mvct_fail(MVCT_EINVAL, "mvct_recon: plan belongs to a batch");
+    if (o.psi_record) return recon_with_psi(P, d_sino, d_weights, beta, n_iter, o, d_img_inout, stats, stream);
     DeviceGuard dg(P->device);
     cudaStream_t st = (cudaStream_t)stream;
     const Geo &g = P->geo;
@@ -798,6 +904,7 @@ extern "C" int mvct_recon(mvct_plan P, const float *d_sino, const float *d_weigh
         a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
         a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
+        a.lambda_rule = o.lambda_rule;
         void *args[] = {&a};
         const void *kern = o.storage == MVCT_STORAGE_BF16  ? (const void *)k_recon<false, __nv_bfloat16>
                            : o.storage == MVCT_STORAGE_F16 ? (const void *)k_recon<false, __half>
@@ -1036,12 +1143,14 @@ extern "C" int mvct_batch_bind(mvct_batch b, const float *const *d_sinos, const 
     mvct_recon_opts o;
     if (opts_in) o = *opts_in;
     else mvct_recon_opts_init(&o);
-    if (o.lambda_schedule || o.state || o.d_best_out || o.subset_order)
-        return mvct_fail(MVCT_EINVAL,
-                         "mvct_batch_bind: lambda_schedule, state, d_best_out and subset_order are one-slice options");
+    if (o.lambda_schedule || o.state || o.d_best_out || o.subset_order || o.psi_record)
+        return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: lambda_schedule, state, d_best_out, subset_order and "
+                         "psi_record are one-slice options");
     if (!mvct_eps_ok(o.tv_eps) || !std::isfinite(o.kappa) || !std::isfinite(o.lambda0) ||
         !std::isfinite(o.mu0) || !(o.barrier_timeout_ms > 0) ||
-        (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON))
+        (o.data_term != MVCT_DATA_WLS && o.data_term != MVCT_DATA_POISSON) ||
+        (o.lambda_rule != MVCT_LAMBDA_SUBSET && o.lambda_rule != MVCT_LAMBDA_PASS &&
+         o.lambda_rule != MVCT_LAMBDA_PASS_SLIDING))
         return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: invalid options");
     if (o.storage != MVCT_STORAGE_F32) return mvct_fail(MVCT_EINVAL, "mvct_batch_bind: only FP32 storage");
     for (int i = 0; i < b->count; ++i) {
@@ -1146,6 +1255,7 @@ extern "C" int mvct_batch_run(mvct_batch b, int32_t n_iter, void *stream)
         a.spin_cap = std::max<unsigned long long>(a.timeout_ns / 50ull, 1000ull);
         a.debug_unreachable = o.debug_unreachable_barrier ? 1 : 0;
         a.poisson = o.data_term == MVCT_DATA_POISSON ? 1 : 0;
+        a.lambda_rule = o.lambda_rule;
         cudaError_t le;
         if (b->param_kernel) {
             // descriptors in the kernel parameters (copied at launch, captured by graphs)

@@ -54,6 +54,7 @@ class ReconState(ctypes.Structure):
         ("best_pass", ctypes.c_double),
         ("best_n", ctypes.c_int64),
         ("phi_ring", ctypes.c_double * MVCT_MAX_SUBSETS),
+        ("pass_prev", ctypes.c_double),
     ]
 
 
@@ -75,7 +76,13 @@ class ReconOpts(ctypes.Structure):
         ("data_term", ctypes.c_int32),
         ("storage", ctypes.c_int32),
         ("subset_order", ctypes.POINTER(ctypes.c_int32)),
+        ("lambda_rule", ctypes.c_int32),
+        ("psi_record", ctypes.POINTER(ctypes.c_double)),
     ]
+
+
+# which square differences drive Eq. 4-5 under ordered subsets (mvct.h MVCT_LAMBDA_*)
+LAMBDA_RULES = {"subset": 0, "pass": 1, "pass_sliding": 2}
 
 
 class ReconStats(ctypes.Structure):
@@ -253,6 +260,7 @@ class ReconResult:
     grid_blocks: int
     forward_ms: float = 0.0
     back_ms: float = 0.0
+    psi: Optional[np.ndarray] = None   # Psi after every pass (psi_record=True)
 
 
 class Plan:
@@ -333,8 +341,9 @@ class Plan:
     def recon(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter: int,
               img: Optional[torch.Tensor] = None, init_from_input: bool = False,
               best_out: Optional[torch.Tensor] = None, lambda_schedule=None,
-              state: Optional[ReconState] = None, stream=None, **opts):
-        """Run ``mvct_recon``; returns (image tensor, ReconResult)."""
+              state: Optional[ReconState] = None, stream=None, psi_record: bool = False, **opts):
+        """Run ``mvct_recon``; returns (image tensor, ReconResult). psi_record: also
+        return Psi of the iterate after every pass (ReconResult.psi)."""
         R = self.V * self.C
         if img is None:
             img = torch.zeros((self.n, self.n), device=p.device, dtype=torch.float32)
@@ -342,6 +351,8 @@ class Plan:
         lib().mvct_recon_opts_init(ctypes.byref(o))
         if isinstance(opts.get("storage"), str):
             opts = dict(opts, storage=STORAGE[opts["storage"]])
+        if isinstance(opts.get("lambda_rule"), str):
+            opts = dict(opts, lambda_rule=LAMBDA_RULES[opts["lambda_rule"]])
         order = None
         if opts.get("subset_order") is not None:
             order = np.ascontiguousarray(opts["subset_order"], dtype=np.int32)
@@ -361,6 +372,10 @@ class Plan:
             o.lambda_schedule = sched.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         if state is not None:
             o.state = ctypes.pointer(state)
+        psi = None
+        if psi_record:
+            psi = np.full(n_iter // self.S + 1, np.nan)
+            o.psi_record = psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         phi = np.zeros(max(n_iter, 1))
         lam = np.zeros(max(n_iter, 1))
         st = ReconStats()
@@ -370,7 +385,7 @@ class Plan:
                                 ctypes.byref(o), _dev_f32(img, self.n * self.n, "img"),
                                 ctypes.byref(st), ctypes.c_void_p(_stream(stream))))
         return img, ReconResult(phi[:n_iter], lam[:n_iter], st.best_n, st.best_pass, st.loop_ms,
-                                st.setup_ms, st.grid_blocks, st.forward_ms, st.back_ms)
+                                st.setup_ms, st.grid_blocks, st.forward_ms, st.back_ms, psi)
 
 
 def _plan_tune(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter_probe: int = 40, stream=None) -> dict:
@@ -451,6 +466,8 @@ class Batch:
         N = [p.n * p.n for p in self.plans]
         o = ReconOpts()
         lib().mvct_recon_opts_init(ctypes.byref(o))
+        if isinstance(opts.get("lambda_rule"), str):
+            opts = dict(opts, lambda_rule=LAMBDA_RULES[opts["lambda_rule"]])
         for k, v in opts.items():
             if not hasattr(o, k):
                 raise TypeError(f"unknown option {k}")

@@ -190,10 +190,12 @@ def _torch():
 
 
 def make_pairs(seeds, device, width: int = 96, n_iter: int = N_ITER_TARGET, workers: int = 8, log=None,
-               kind: str = "full"):
+               kind: str = "full", target_opts=None):
     """(FBP images, n_iter-iteration OS-TV images from the FBP start) for the
     seeded cases, both [N][n][n] FP32 on `device`: the pairs the network learns.
-    The host generates the next chunk of cases while the GPU reconstructs one."""
+    `target_opts`: loop options of the target reconstructions (default: the
+    library's). The host generates the next chunk of cases while the GPU
+    reconstructs one."""
     import concurrent.futures as cf
     import multiprocessing as mp
     import time
@@ -222,7 +224,8 @@ def make_pairs(seeds, device, width: int = 96, n_iter: int = N_ITER_TARGET, work
             rec.load(cases)
             for k in range(len(cases)):
                 rec.fbp(k, X[done + k])
-            out = rec.run(len(cases), [c.beta for c in cases], [X[done + k] for k in range(len(cases))], n_iter)
+            out = rec.run(len(cases), [c.beta for c in cases], [X[done + k] for k in range(len(cases))], n_iter,
+                          **dict(target_opts or {}))
             for k in range(len(cases)):
                 Y[done + k].copy_(out[k])
             torch.cuda.synchronize()
@@ -471,30 +474,18 @@ def load_weights(path: Optional[str] = None) -> np.ndarray:
     return p
 
 
-def _main(argv=None):
-    import argparse
+def _train_main(args):
     import json
     import os
     import sys
     import time
 
-    ap = argparse.ArgumentParser(description="train the warm-start network on pairs the method generates")
-    ap.add_argument("--pairs", type=int, default=2000)
-    ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--batch", type=int, default=16)
-    ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--lr-final", type=float, default=None, help="cosine decay of the step size to this value")
-    ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--width", type=int, default=96, help="slices per batched reconstruction")
-    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
-    ap.add_argument("--out", default=weights_path())
-    args = ap.parse_args(argv)
     torch = _torch()
     dev = torch.device("cuda", torch.cuda.current_device())
     log = lambda s: print(s, file=sys.stderr, flush=True)
     t0 = time.perf_counter()
-    X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width, workers=args.workers,
-                          log=log)
+    X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width,
+                          n_iter=args.target_iterations, workers=args.workers, log=log)
     t1 = time.perf_counter()
     cnn = CNN(args.batch, X.shape[1], X.shape[2], init_params(args.seed))
     hist = train(cnn, X, Y, args.epochs, args.batch, args.lr, args.seed, log, lr_final=args.lr_final)
@@ -505,13 +496,78 @@ def _main(argv=None):
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     np.save(args.out, params)
     rec = dict(pairs=args.pairs, train_seeds=[TRAIN_SEED0, TRAIN_SEED0 + args.pairs - 1], epochs=args.epochs,
-               batch=args.batch, lr=args.lr, lr_final=args.lr_final, seed=args.seed, target_iterations=N_ITER_TARGET,
+               batch=args.batch, lr=args.lr, lr_final=args.lr_final, seed=args.seed,
+               target_iterations=args.target_iterations, target_options="the library defaults",
                epoch_loss=hist, pair_generation_s=t1 - t0, pair_timing=tp, training_s=t2 - t1,
                steps=args.epochs * (args.pairs // args.batch))
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(rec, f, indent=1)
     print(json.dumps(rec))
     return 0
+
+
+def _evaluate_main(args):
+    """Held-out evaluation on the GPU: per seed the plain form (FBP start, 500
+    sub-iterations) against network start + K and FBP start + K sub-iterations,
+    judged by the objective Psi (mvct_objective, FP64 reduction; pinned against
+    the FP64 oracle by the tests); one JSON line: the summary per start and K
+    and, with --per-seed, every seed's values."""
+    import json
+    import os
+    import time
+
+    torch = _torch()
+    seeds = list(range(args.seed0, args.seed0 + args.seeds))
+    t0 = time.perf_counter()
+    cases = make_cases(seeds, workers=args.workers)
+    t_gen = time.perf_counter() - t0
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cnn = CNN(16, cases[0].geom.n, cases[0].geom.n, load_weights(args.weights))
+    warm = {} if args.lambda0 is None else {"lambda0": args.lambda0}
+    t0 = time.perf_counter()
+    res = evaluate(cnn, cases, args.Ks, dev, width=args.width, warm_opts=warm)
+    t_gpu = time.perf_counter() - t0
+    cnn.close()
+    line = dict(seeds=[seeds[0], seeds[-1]], Ks=args.Ks, warm_opts=warm,
+                weights=os.path.basename(args.weights or weights_path()),
+                summary=summarize(res, args.Ks), host_gen_s=t_gen, gpu_eval_s=t_gpu)
+    if args.per_seed:
+        line["per_seed"] = res
+    print(json.dumps(line))
+    return 0
+
+
+def _main(argv=None):
+    """``python -m paper_1903_10088_gb300.warmstart [train] [--pairs ...]`` trains the
+    network on pairs the method generates; ``... evaluate [--seeds 200 ...]`` runs
+    the held-out evaluation."""
+    import argparse
+    import os
+    import sys
+
+    argv = list(sys.argv[1:] if argv is None else argv)
+    mode = argv.pop(0) if argv and argv[0] in ("train", "evaluate") else "train"
+    ap = argparse.ArgumentParser(prog=f"warmstart {mode}")
+    ap.add_argument("--width", type=int, default=96 if mode == "train" else 48,
+                    help="slices per batched reconstruction")
+    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    if mode == "train":
+        ap.add_argument("--pairs", type=int, default=2000)
+        ap.add_argument("--epochs", type=int, default=20)
+        ap.add_argument("--batch", type=int, default=16)
+        ap.add_argument("--lr", type=float, default=1e-3)
+        ap.add_argument("--lr-final", type=float, default=None, help="cosine decay of the step size to this value")
+        ap.add_argument("--seed", type=int, default=0)
+        ap.add_argument("--target-iterations", type=int, default=N_ITER_TARGET)
+        ap.add_argument("--out", default=weights_path())
+        return _train_main(ap.parse_args(argv))
+    ap.add_argument("--weights", default=None)
+    ap.add_argument("--seeds", type=int, default=200)
+    ap.add_argument("--seed0", type=int, default=HELDOUT_SEED0)
+    ap.add_argument("--Ks", type=int, nargs="+", default=[25, 50, 100])
+    ap.add_argument("--lambda0", type=float, default=None, help="lambda0 of the network-started runs")
+    ap.add_argument("--per-seed", action="store_true")
+    return _evaluate_main(ap.parse_args(argv))
 
 
 if __name__ == "__main__":

@@ -43,6 +43,12 @@ def test_binding_covers_every_declared_symbol():
     assert set(header_functions()) <= set(mvct.EXPORTS)
 
 
+def oracle_default_rule():
+    import oracle
+
+    return oracle.LAMBDA_RULES[oracle.DEFAULTS["lambda_rule"]]
+
+
 def test_struct_layouts_match_header(libmvct):
     """The opts defaults come back through ctypes with the paper's constants, which
     only works if the binding's struct layout matches the header's."""
@@ -51,7 +57,8 @@ def test_struct_layouts_match_header(libmvct):
     o = mvct.ReconOpts()
     libmvct.mvct_recon_opts_init(ctypes.byref(o))
     assert (o.lambda0, o.dlambda_up, o.dlambda_down) == (0.01, 1e-4, 2e-4)
-    assert (o.mu0, o.kappa, o.tv_eps, o.barrier_timeout_ms) == (0.05, 100.0, 1e-6, 2000.0)
+    assert (o.mu0, o.kappa, o.tv_eps, o.barrier_timeout_ms) == (0.05, 50.0, 1e-6, 2000.0)
+    assert o.lambda_rule == mvct.LAMBDA_RULES["pass_sliding"] == oracle_default_rule()
     assert o.init_from_input == 0 and not o.d_best_out and not o.lambda_schedule
 
 

@@ -168,3 +168,24 @@ def test_recon_argument_errors(mvct):
         st.n_done = 5
         with pytest.raises(mvct.MvctError):
             plan.recon(cuda(c.p), cuda(c.w), c.beta, 2, state=st)
+
+
+def test_psi_record_every_pass(mvct):
+    """The convergence record (Sec. 4.2 plots the square difference per
+    iteration; the full objective after every pass is kept here): Psi of the
+    start image and of the iterate after every pass equals the oracle's objective
+    of the oracle's own iterates after the same number of sub-iterations (1e-5),
+    and recording it changes nothing in the run (pass-by-pass resume is bitwise)."""
+    c = ph.make_case("small", 12)
+    S, N = c.n_subsets, 30
+    with mvct.Plan(c.geom, S) as plan:
+        a, ra = plan.recon(cuda(c.p), cuda(c.w), c.beta, N)
+        b, rb = plan.recon(cuda(c.p), cuda(c.w), c.beta, N, psi_record=True)
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+        assert np.array_equal(ra.lam, rb.lam) and np.array_equal(ra.phi, rb.phi)
+        assert rb.psi.shape == (N // S + 1,)
+    for k in range(N // S + 1):
+        ref = oracle.recon(c.geom, S, c.p, c.w, c.beta, k * S)
+        psi = oracle.objective(c.geom, ref["image"], c.p, c.w, c.beta, c.tv_eps)
+        assert abs(rb.psi[k] - psi) <= 1e-5 * psi, k
+    assert np.all(np.diff(rb.psi) < 0)

@@ -248,7 +248,7 @@ def test_paper_constants_are_the_defaults():
 
 def test_lambda_rule_and_best_iterate_follow_eq4_eq5():
     c = ph.make_case("small", 1)
-    r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, 40, want_best=True)
+    r = oracle.recon(c.geom, c.n_subsets, c.p, c.w, c.beta, 40, want_best=True, lambda_rule="subset")
     phi, lam = r["phi"], r["lam"]
     assert lam[0] == 0.01
     for k in range(1, len(phi)):
@@ -279,6 +279,71 @@ def test_lambda_replay_reproduces_the_adaptive_run():
     assert rel(r2["image"], r["image"]) > 1e-3
 
 
+def _eq45(lam_prev, now, before):
+    """Eq. 4-5 with the paper's constants and the floor: one decision."""
+    if now < before:
+        lam = lam_prev + 1e-4
+    elif now > before:
+        lam = lam_prev - 2e-4
+    else:
+        lam = lam_prev
+    return max(lam, 1e-4)
+
+
+def test_pass_rules_follow_their_comparisons():
+    """The two pass readings of Sec. 3.3.2 under ordered subsets, checked on the
+    run's own square differences: "pass_sliding" compares Phi_n with Phi_{n-S}
+    (the pass sums P_n and P_{n-1}) from n = S on and keeps lambda0 during the
+    first pass; "pass" decides once per pass, at n = kS (k >= 2), on the sums of
+    the last two complete passes, and keeps lambda between decisions."""
+    c = ph.make_case("small", 2)
+    S, N = 4, 36
+    r = oracle.recon(c.geom, S, c.p, c.w, c.beta, N, lambda_rule="pass_sliding")
+    phi, lam = r["phi"], r["lam"]
+    assert np.all(lam[:S] == 0.01)
+    for n in range(S, N):
+        assert lam[n] == _eq45(lam[n - 1], phi[n], phi[n - S])
+    assert np.any(lam != 0.01)
+    r = oracle.recon(c.geom, S, c.p, c.w, c.beta, N, lambda_rule="pass")
+    phi, lam = r["phi"], r["lam"]
+    assert np.all(lam[:2 * S] == 0.01)
+    for n in range(2 * S, N):
+        if n % S:
+            assert lam[n] == lam[n - 1]
+        else:
+            now = sum(phi[k] for k in range(n - S, n))
+            before = sum(phi[k] for k in range(n - 2 * S, n - S))
+            assert lam[n] == _eq45(lam[n - 1], now, before)
+    assert np.any(lam != 0.01)
+
+
+def test_pass_readings_coincide_with_the_subset_reading_without_subsets():
+    """With one subset (S = 1) the pass of the sliding reading is one sub-iteration,
+    so it compares Phi_n with Phi_{n-1} exactly like the subset reading: the runs
+    are identical bit for bit; and every reading gives the same first pass."""
+    c = ph.make_case("small", 3, geom=ph.Geometry(n=48, n_views=40, n_channels=60))
+    a = oracle.recon(c.geom, 1, c.p, c.w, c.beta, 12, lambda_rule="subset")
+    b = oracle.recon(c.geom, 1, c.p, c.w, c.beta, 12, lambda_rule="pass_sliding")
+    assert np.array_equal(a["image"], b["image"]) and np.array_equal(a["lam"], b["lam"])
+    S = 4
+    runs = [oracle.recon(c.geom, S, c.p, c.w, c.beta, S, lambda_rule=rule)
+            for rule in ("subset", "pass", "pass_sliding")]
+    # during the first pass the pass readings hold lambda0; with lambda replayed the
+    # subset reading's run is the same arithmetic
+    for r in runs[1:]:
+        assert np.array_equal(r["image"], runs[1]["image"])
+    rep = oracle.recon(c.geom, S, c.p, c.w, c.beta, S, lambda_schedule=np.full(S, 0.01), lambda_rule="subset")
+    assert np.array_equal(rep["image"], runs[1]["image"])
+
+
+@pytest.mark.parametrize("rule", ["pass", "pass_sliding"])
+def test_lambda_replay_reproduces_each_pass_rule(rule):
+    c = ph.make_case("small", 4)
+    r = oracle.recon(c.geom, 5, c.p, c.w, c.beta, 30, lambda_rule=rule)
+    rep = oracle.recon(c.geom, 5, c.p, c.w, c.beta, 30, lambda_schedule=r["lam"], lambda_rule=rule)
+    assert np.array_equal(r["image"], rep["image"])
+
+
 def test_first_step_is_preconditioned_gradient_step(A8):
     """One sub-iteration with S subsets equals mu0 - tau D (S A_s^T W_s (A_s mu0 - p_s)
     + beta grad TV), clamped at 0, with A_s taken from the brute-force matrix."""
@@ -294,7 +359,8 @@ def test_first_step_is_preconditioned_gradient_step(A8):
     ws, ps = w[0::S].ravel(), p[0::S].ravel()
     g = As.T @ (ws * (As @ mu0.ravel() - ps))
     _, tvg = oracle.tv(mu0, 1e-6)
-    expect = np.maximum(0.0, mu0.ravel() - 100 * lam * D.ravel() * (S * g + beta * tvg.ravel()))
+    kappa = oracle.DEFAULTS["kappa"]
+    expect = np.maximum(0.0, mu0.ravel() - kappa * lam * D.ravel() * (S * g + beta * tvg.ravel()))
     assert np.abs(r["image"].ravel() - expect).max() < 1e-13
     assert abs(r["phi"][0] - np.sum((As @ mu0.ravel() - ps) ** 2)) < 1e-12 * r["phi"][0]
 
@@ -307,7 +373,7 @@ def test_objective_decreases_monotonically_at_small_step():
     prev = None
     img = None
     for k in range(12):
-        r = oracle.recon(g, 1, c.p, c.w, c.beta, 1, init=img, lambda_schedule=[0.005])
+        r = oracle.recon(g, 1, c.p, c.w, c.beta, 1, init=img, lambda_schedule=[0.5 / oracle.DEFAULTS["kappa"]])
         img = r["image"]
         psi = oracle.objective(g, img, c.p, c.w, c.beta, 1e-6)
         if prev is not None:
@@ -354,7 +420,7 @@ def test_poisson_gradient_matches_finite_differences(A8):
 
     h = 1e-6
     grad = np.array([(nll(mu0.ravel() + h * e) - nll(mu0.ravel() - h * e)) / (2 * h) for e in np.eye(64)])
-    expect = np.maximum(0.0, mu0.ravel() - 100 * lam * D.ravel() * grad)
+    expect = np.maximum(0.0, mu0.ravel() - oracle.DEFAULTS["kappa"] * lam * D.ravel() * grad)
     assert np.abs(r["image"].ravel() - expect).max() < 1e-8
 
 
@@ -392,7 +458,8 @@ def test_subset_order_first_steps_use_the_listed_subsets(A8):
     As = A3[2::S].reshape(-1, 64)
     g = As.T @ (w[2::S].ravel() * (As @ mu0.ravel() - p[2::S].ravel()))
     _, tvg = oracle.tv(mu0, 1e-6)
-    expect = np.maximum(0.0, mu0.ravel() - 100 * lam * D.ravel() * (S * g + beta * tvg.ravel()))
+    kappa = oracle.DEFAULTS["kappa"]
+    expect = np.maximum(0.0, mu0.ravel() - kappa * lam * D.ravel() * (S * g + beta * tvg.ravel()))
     assert np.abs(r1["image"].ravel() - expect).max() < 1e-13
     r2 = oracle.recon(G8, S, p, w, beta, 2, init=mu0, lambda_schedule=[lam, lam], subset_order=order)
     A0 = A3[0::S].reshape(-1, 64)
