@@ -851,6 +851,75 @@ def run_subsets(args):
     return 0
 
 
+def run_ops(args):
+    """Per-operator timing of the C ABI (CUDA events, warm caches, seeded random
+    inputs): mvct_forward / mvct_back on one subset and on all views,
+    mvct_tv_grad, mvct_objective, mvct_fbp, and the warm-start network (forward,
+    and one Adam step, on a batch of --cnn-batch images). One JSON object; also
+    the command that the operators' profiler captures run."""
+    import torch
+
+    from paper_1903_10088_gb300 import mvct
+
+    mvct.lib()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g = ph.Geometry(n=args.n, n_views=args.views, n_channels=args.channels)
+    rng = np.random.default_rng(0)
+    img = torch.from_numpy(rng.uniform(0, 0.1, (g.n, g.n)).astype(np.float32)).cuda()
+    sino = torch.from_numpy(rng.uniform(0, 1, (g.n_views, g.n_channels)).astype(np.float32)).cuda()
+    w = torch.from_numpy(rng.uniform(0.1, 1, (g.n_views, g.n_channels)).astype(np.float32)).cuda()
+    Vs = g.n_views // args.subsets_ops
+    sub = sino[:Vs].contiguous()
+    out = {"workload": "operators of the C ABI on seeded random inputs",
+           "geometry": dict(n=g.n, views=g.n_views, channels=g.n_channels, subsets=args.subsets_ops), "ms": {}}
+    ops = args.ops.split(",")
+    with mvct.Plan(g, args.subsets_ops) as plan:
+        q_sub = torch.empty((Vs, g.n_channels), device="cuda")
+        q_all = torch.empty((g.n_views, g.n_channels), device="cuda")
+        b = torch.empty((g.n, g.n), device="cuda")
+        if "forward" in ops:
+            out["ms"]["forward_subset"] = timed(lambda: plan.forward(img, 0, out=q_sub), args.reps)
+            out["ms"]["forward_all"] = timed(lambda: plan.forward(img, -1, out=q_all), args.reps)
+        if "back" in ops:
+            out["ms"]["back_subset"] = timed(lambda: plan.back(sub, 0, out=b), args.reps)
+            out["ms"]["back_all"] = timed(lambda: plan.back(sino, -1, out=b), args.reps)
+        if "tv" in ops:
+            out["ms"]["tv_grad"] = timed(lambda: plan.tv_grad(img, 1e-6), args.reps)
+        if "objective" in ops:
+            out["ms"]["objective"] = timed(lambda: plan.objective(img, sino, w, 1e-3, 1e-6), args.reps)
+        if "fbp" in ops:
+            out["ms"]["fbp"] = timed(lambda: plan.fbp(sino, out=b), args.reps)
+    if "cnn" in ops:
+        from paper_1903_10088_gb300 import warmstart as wst
+
+        N = args.cnn_batch
+        x = torch.from_numpy(rng.uniform(0, 0.1, (N, g.n, g.n)).astype(np.float32)).cuda()
+        y = 0.9 * x
+        xo = torch.empty_like(x)
+        net = wst.CNN(N, g.n, g.n, wst.init_params(0))
+        out["ms"]["cnn_forward"] = timed(lambda: net.forward(x, out=xo), args.reps)
+        out["ms"]["cnn_train_step"] = timed(lambda: net.train_step(x, y, 1e-5), args.reps)
+        net.close()
+        flops = 2.0 * N * g.n * g.n * (6 * 9 * 32 * 32 + 2 * 9 * 32)
+        out["cnn_batch"] = N
+        out["cnn_forward_tflops"] = flops / out["ms"]["cnn_forward"] / 1e9
+        out["cnn_train_tflops"] = 3 * flops / out["ms"]["cnn_train_step"] / 1e9
+    print(json.dumps(out))
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -864,7 +933,14 @@ def main(argv=None):
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven stack")
     ap.add_argument("--ref-threads", type=int, default=0,
                     help="oracle threads for the whole-slice CPU timing (0: every host core)")
-    ap.add_argument("--workload", choices=["plain", "batched", "subsets"], default="plain")
+    ap.add_argument("--workload", choices=["plain", "batched", "subsets", "ops"], default="plain")
+    ap.add_argument("--ops", default="forward,back,tv,objective,fbp,cnn", help="--workload ops: which operators")
+    ap.add_argument("--reps", type=int, default=20, help="--workload ops: timed calls per operator")
+    ap.add_argument("--cnn-batch", type=int, default=16, help="--workload ops: images per network call")
+    ap.add_argument("--n", type=int, default=512, help="--workload ops: image side")
+    ap.add_argument("--views", type=int, default=800, help="--workload ops: views")
+    ap.add_argument("--channels", type=int, default=738, help="--workload ops: channels")
+    ap.add_argument("--subsets-ops", type=int, default=20, help="--workload ops: subsets")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
@@ -872,6 +948,8 @@ def main(argv=None):
         return run_batched(args)
     if args.workload == "subsets":
         return run_subsets(args)
+    if args.workload == "ops":
+        return run_ops(args)
     return run_ours(args)
 
 

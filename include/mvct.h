@@ -109,10 +109,10 @@ typedef struct mvct_recon_opts {
                                       per launch, resumed bit for bit. mvct_recon only */
 } mvct_recon_opts;
 
-/* Readings of Eq. 4-5 under ordered subsets. Sec. 3.3.2 raises lambda when "the
- * square of difference between a reprojection and a projection" decreases and
- * lowers it when it increases; with subsets each sub-iteration n only has the
- * square difference Phi_n of its own subset's rays. The rules say which values
+/* Readings of Eq. 4-5 under ordered subsets. Sec. 3.3.2 raises lambda while the
+ * squared difference between reprojection and measured projection falls and
+ * lowers it when that difference grows; with subsets each sub-iteration n only
+ * has the square difference Phi_n of its own subset's rays. The rules say which values
  * are compared (lambda unchanged on a tie and where no comparison is made):
  *   SUBSET        Phi_n with Phi_{n-1}, n >= 1 (consecutive sub-iterations, i.e.
  *                 different subsets);
@@ -164,7 +164,7 @@ typedef struct mvct_recon_stats {
 void mvct_recon_opts_init(mvct_recon_opts *opts);
 
 /* Build a plan for geometry *g with n_subsets ordered subsets (Sec. 3.4:
- * thinning with an equal interval; n_views % n_subsets must be 0). Allocates
+ * views thinned at a fixed spacing; n_views % n_subsets must be 0). Allocates
  * the ray and view tables and scratch on the CURRENT device and computes the
  * support mask (A^T 1 > 0) there; synchronous. *out receives the plan. */
 int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_plan *out);
@@ -199,6 +199,17 @@ int mvct_tv_grad(mvct_plan plan, const float *d_img, double eps, float *d_grad,
  * d_sino, d_weights: V*C; d_out: one double (device). */
 int mvct_objective(mvct_plan plan, const float *d_img, const float *d_sino, const float *d_weights,
                    double beta, double eps, double *d_out, void *stream);
+
+/* Gradient of the objective over all views (the direction Eq. 3 steps along,
+ * in the weighted-least-squares reading of Eq. 2):
+ *   d_grad = A^T (w .* (A img - p)) + beta grad TV_eps(img)        (FP32, n*n),
+ * and, if d_out_or_null is given, Psi(img) as mvct_objective computes it (one
+ * device double, FP64 reduction). Projection and backprojection are the plan's
+ * matched pair (mvct_forward / mvct_back), the TV gradient that of mvct_tv_grad.
+ * d_sino, d_weights: V*C; d_grad must not alias d_img. Uses the plan's scratch;
+ * asynchronous on stream. */
+int mvct_objective_grad(mvct_plan plan, const float *d_img, const float *d_sino, const float *d_weights,
+                        double beta, double eps, float *d_grad, double *d_out_or_null, void *stream);
 
 /* The ordered-subset TV reconstruction (Eq. 3-5, Sec. 3.3.2, 3.4, 4.2).
  * d_sino: measured log projections p [V][C]; d_weights: statistical weights w

@@ -23,7 +23,7 @@
  *   Gradient step (Eq. 3) with adaptive lambda (Eq. 4-5, lambda0 = 0.01,
  *     +1e-4 when the square difference falls, -2e-4 when it rises).
  *   Homogeneous initial image mu0 (Sec. 3.3.2).
- *   Ordered subsets by thinning the views with an equal interval; the
+ *   Ordered subsets by thinning the views at a fixed spacing; the
  *     regulariser weight multiplied by the thinning parameter 1/S (Sec. 3.4).
  *   Best iterate at the minimum of the oscillating square difference (Sec. 4.2).
  *
@@ -79,8 +79,9 @@ typedef struct {
     int32_t lambda_rule;    /* which square difference drives Eq. 4-5 (see oracle_recon) */
 } oracle_recon_params;
 
-/* Readings of "the objective function being the square of difference between a
- * reprojection and a projection" (Sec. 3.3.2) under ordered subsets. */
+/* Readings of Sec. 3.3.2 (lambda follows the squared difference between the
+ * reprojection and the measured projection) under ordered subsets, where a
+ * sub-iteration sees only its own subset (Sec. 3.4). */
 enum {
     LAMBDA_SUBSET = 0,       /* Phi_n against Phi_{n-1}: consecutive sub-iterations (different subsets) */
     LAMBDA_PASS = 1,         /* once per pass: the sum over the last complete pass against the pass before */
@@ -190,7 +191,7 @@ static void joseph_ray_transpose(const oracle_geometry *g, double value, int v, 
 
 /* Number of rows of a subset's sinogram and the view held in row k.
  * subset < 0: all views in natural order. Otherwise views v = subset + k*S
- * (Sec. 3.4: thinning with an equal interval). */
+ * (Sec. 3.4: views thinned at a fixed spacing). */
 static int subset_rows(const oracle_geometry *g, int subset, int n_subsets)
 {
     return subset < 0 ? g->n_views : g->n_views / n_subsets;

@@ -331,9 +331,36 @@ extern "C" int mvct_objective(mvct_plan P, const float *d_img, const float *d_si
     cudaStream_t st = (cudaStream_t)stream;
     float *img = pad_row0(P->pad[0], P->geo.n), *imgT = pad_row0(P->pad[2], P->geo.n);
     CK(launch_pad_transpose(d_img, img, imgT, P->geo.n, st));
-    CK(launch_residual(P, img, imgT, d_sino, d_weights, P->partials, st));
+    CK(launch_residual(P, img, imgT, d_sino, d_weights, P->partials, nullptr, st));
     CK(launch_tv(P, d_img, (float)eps, nullptr, P->partials2, st));
     CK(launch_final_sum(P->partials, P->reduce_grid, 0.5, P->partials2, P->reduce_grid, beta, d_out, st));
+    return MVCT_OK;
+}
+
+extern "C" int mvct_objective_grad(mvct_plan P, const float *d_img, const float *d_sino, const float *d_weights,
+                                   double beta, double eps, float *d_grad, double *d_out_or_null, void *stream)
+{
+    if (!P) return mvct_fail(MVCT_EINVAL, "mvct_objective_grad: null plan");
+    int rc = mvct_check_ptrs(P->device, stream, "mvct_objective_grad", {d_img, d_sino, d_weights, d_grad});
+    if (rc == MVCT_OK && d_out_or_null) rc = mvct_check_ptrs(P->device, stream, "mvct_objective_grad", {d_out_or_null});
+    if (rc) return rc;
+    if (!mvct_eps_ok(eps) || !std::isfinite(beta))
+        return mvct_fail(MVCT_EINVAL, "mvct_objective_grad: invalid beta/eps");
+    if (d_grad == d_img) return mvct_fail(MVCT_EINVAL, "mvct_objective_grad: d_grad must not alias d_img");
+    DeviceGuard dg(P->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int n = P->geo.n;
+    float *img = pad_row0(P->pad[0], n), *imgT = pad_row0(P->pad[2], n);
+    float *tvg = pad_row0(P->pad[1], n); // scratch outside mvct_recon
+    CK(launch_pad_transpose(d_img, img, imgT, n, st));
+    // e = w .* (A img - p) over all views, and sum w r^2 (FP64)
+    CK(launch_residual(P, img, imgT, d_sino, d_weights, P->partials, P->sino_tmp, st));
+    CK(launch_back(P, P->sino_tmp, d_grad, -1, st));                 // A^T e
+    CK(launch_tv(P, d_img, (float)eps, tvg, P->partials2, st));      // grad TV_eps
+    CK(launch_axpy(P, d_grad, tvg, (float)beta, (size_t)n * n, st));
+    if (d_out_or_null)
+        CK(launch_final_sum(P->partials, P->reduce_grid, 0.5, P->partials2, P->reduce_grid, beta, d_out_or_null,
+                            st));
     return MVCT_OK;
 }
 

@@ -2,10 +2,11 @@
 // ReLU after layers 1-7, residual output out = x + f(x)) that maps a scaled FBP
 // image to a scaled start image for the OS-TV loop. BF16 weights and
 // activations, FP32 accumulation, hand-written forward and backward kernels:
-//  * 32 -> 32 layers: BF16 tensor-core tiles (mma.sync m16n8k16, FP32 accumulate)
-//    for the forward convolution, the input gradient (the same kernel with the
-//    flipped, transposed kernel) and the weight gradient (pixels as the reduction
-//    dimension, per-block partials summed in a fixed order);
+//  * 32 -> 32 layers: the forward convolution and the input gradient (the same
+//    kernel with the flipped, transposed kernel) on the 5th-generation tensor
+//    cores (tcgen05.mma into TMEM, mvct_cnn_tc.cuh); the weight gradient (pixels
+//    as the reduction dimension, per-block partials summed in a fixed order) on
+//    mma.sync m16n8k16 tiles, FP32 accumulate;
 //  * the 1 -> 32 and 32 -> 1 layers: CUDA-core FP32 arithmetic on BF16 data;
 //  * fused mean-squared-error loss and Adam.
 // Every reduction has a fixed order: training is deterministic.
@@ -68,86 +69,6 @@ __device__ __forceinline__ size_t apix(int n, int y, int x, int H, int W)
 {
     // padded pixel index of image pixel (y, x) (y, x may be -1 .. H / W)
     return ((size_t)n * (H + 2) + (y + 1)) * (W + 2) + (x + 1);
-}
-
-// ---- 32 -> 32 convolution on tensor cores ---------------------------------
-// MODE 0 (forward): out = relu(conv(in, wk) + bias).
-// MODE 1 (input gradient): out = conv(in, wk) * [mask > 0] (in = the layer's
-// pre-activation gradient, wk = flipped transposed kernel, mask = the previous
-// layer's activation). wk: [9][32 n][32 k] BF16 (n = output, k = input channel).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_conv32(const __nv_bfloat16 *__restrict__ in,
-                                                const __nv_bfloat16 *__restrict__ wk,
-                                                const float *__restrict__ bias,
-                                                const __nv_bfloat16 *__restrict__ mask,
-                                                __nv_bfloat16 *__restrict__ out, int H, int W)
-{
-    __shared__ __align__(16) __nv_bfloat16 s_in[(TH + 2) * (TW + 2) * SPAD];
-    __shared__ __align__(16) __nv_bfloat16 s_w[9 * CH * SPAD];
-    const int n = blockIdx.z, y0 = blockIdx.y * TH, x0 = blockIdx.x * TW;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // input tile with halo: padded rows y0 .. y0 + TH + 1, columns x0 .. x0 + TW + 1
-    for (int k = tid; k < (TH + 2) * (TW + 2) * 4; k += 256) {
-        const int px = k >> 2, q = k & 3;
-        const int ty = px / (TW + 2), tx = px - ty * (TW + 2);
-        const int gy = y0 + ty - 1, gx = x0 + tx - 1; // image coordinates (-1 .. H / W are the border)
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gy <= H && gx <= W) v = *((const uint4 *)(in + apix(n, gy, gx, H, W) * CH) + q);
-        *((uint4 *)(s_in + px * SPAD) + q) = v;
-    }
-    for (int k = tid; k < 9 * CH * 4; k += 256) {
-        const int row = k >> 2, q = k & 3;
-        *((uint4 *)(s_w + row * SPAD) + q) = *((const uint4 *)(wk + (size_t)row * CH) + q);
-    }
-    __syncthreads();
-
-    float acc[4][4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap - 3 * (tap / 3);
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc) {
-            unsigned a0, a1, a2, a3;
-            ldsm_x4(a0, a1, a2, a3,
-                    s_in + ((warp + ky) * (TW + 2) + kx + (lane & 15)) * SPAD + 16 * kc + (lane >> 4) * 8);
-#pragma unroll
-            for (int np = 0; np < 2; ++np) {
-                const int q = lane >> 3;
-                const int nrow = (2 * np + (q >> 1)) * 8 + (lane & 7);
-                unsigned b0, b1, b2, b3;
-                ldsm_x4(b0, b1, b2, b3, s_w + (tap * CH + nrow) * SPAD + 16 * kc + (q & 1) * 8);
-                mma_bf16(acc[2 * np], a0, a1, a2, a3, b0, b1);
-                mma_bf16(acc[2 * np + 1], a0, a1, a2, a3, b2, b3);
-            }
-        }
-    }
-    // epilogue: rows g and g + 8 of the warp's 16 pixels, channels nt*8 + 2t, +1
-    const int g = lane >> 2, t = lane & 3, y = y0 + warp;
-    if (y >= H) return;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int x = x0 + g + 8 * half;
-        if (x >= W) continue;
-        const size_t base = apix(n, y, x, H, W) * CH;
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int co = nt * 8 + 2 * t;
-            float v0 = acc[nt][2 * half], v1 = acc[nt][2 * half + 1];
-            if (MODE == 0) {
-                v0 = fmaxf(v0 + __ldg(bias + co), 0.f);
-                v1 = fmaxf(v1 + __ldg(bias + co + 1), 0.f);
-            } else {
-                const __nv_bfloat162 m = *(const __nv_bfloat162 *)(mask + base + co);
-                v0 = __bfloat162float(m.x) > 0.f ? v0 : 0.f;
-                v1 = __bfloat162float(m.y) > 0.f ? v1 : 0.f;
-            }
-            *(__nv_bfloat162 *)(out + base + co) = __floats2bfloat162_rn(v0, v1);
-        }
-    }
 }
 
 // ---- weight and bias gradient of a 32 -> 32 layer on tensor cores ---------
@@ -534,6 +455,8 @@ __global__ void k_scale(const float *__restrict__ a, float s, float *__restrict_
 } // namespace cnn
 } // namespace mvct
 
+#include "mvct_cnn_tc.cuh" // the 32 -> 32 convolutions on tcgen05 (uses CH and apix above)
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -552,6 +475,8 @@ struct mvct_cnn_s {
     float *part = nullptr;                                                         // weight-gradient partials
     double *loss_part = nullptr, *h_loss = nullptr;
     int part_blocks = 0, steps = 0;
+    int *tc_err = nullptr;   // set by a tensor-core convolution whose wait gave up
+    int tc_grid = 0;         // persistent blocks of the tensor-core convolutions
 };
 
 namespace {
@@ -580,7 +505,8 @@ void free_cnn(mvct_cnn_s *c)
 {
     if (!c) return;
     void *p[] = {c->w,    c->m,    c->v,         c->g,         c->wf,        c->wk_fwd,   c->wk_bwd, c->xs,
-                 c->ys,   c->dout, c->tout,      c->part,      c->loss_part, c->dgrad[0], c->dgrad[1]};
+                 c->ys,   c->dout, c->tout,      c->part,      c->loss_part, c->dgrad[0], c->dgrad[1],
+                 c->tc_err};
     for (void *q : p)
         if (q) cudaFree(q);
     for (auto *a : c->act)
@@ -602,10 +528,10 @@ int cnn_forward(mvct_cnn_s *c, int n, float *out, bool with_target, cudaStream_t
     const int H = c->H, W = c->W;
     const long long pix = (long long)n * H * W;
     k_conv_in<<<grid_for(c, pix, 256), 256, 0, st>>>(c->xs, c->wf + OFF_W1, c->wf + OFF_B1, c->act[0], n, H, W);
-    const dim3 tg((W + TW - 1) / TW, (H + TH - 1) / TH, n);
     for (int l = 0; l < MID; ++l)
-        k_conv32<0><<<tg, 256, 0, st>>>(c->act[l], c->wk_fwd + (size_t)l * 9 * CH * CH, c->wf + OFF_MID + l * MID_SIZE + 9 * CH * CH,
-                                        nullptr, c->act[l + 1], H, W);
+        tc::k_conv32_tc<0><<<c->tc_grid, tc::THREADS, tc::SMEM_BYTES, st>>>(
+            c->act[l], c->wk_fwd + (size_t)l * 9 * CH * CH, c->wf + OFF_MID + l * MID_SIZE + 9 * CH * CH, nullptr,
+            c->act[l + 1], n, H, W, c->tc_err);
     const int gb = grid_for(c, pix, 256);
     k_conv_out<<<gb, 256, 0, st>>>(c->act[6], c->wf + OFF_W8, c->wf + OFF_B8, c->xs, with_target ? c->ys : nullptr, out,
                                    c->dout, with_target ? c->loss_part : nullptr, 1.f / (float)pix, n, H, W);
@@ -623,7 +549,6 @@ int cnn_backward(mvct_cnn_s *c, int n, cudaStream_t st)
     k_dw_edge<1><<<PB, 320, 0, st>>>(c->dout, c->act[6], c->part, n, H, W);
     k_reduce_parts<<<(9 * CH + 1 + 31) / 32, 256, 0, st>>>(c->part, PB, 9 * CH + 1, EDGE_LEN, c->g + OFF_W8);
     k_conv_out_bwd<<<grid_for(c, pix, 256), 256, 0, st>>>(c->dout, c->wf + OFF_W8, c->act[6], c->dgrad[0], n, H, W);
-    const dim3 tg((W + TW - 1) / TW, (H + TH - 1) / TH, n);
     int cur = 0;
     for (int l = MID - 1; l >= 0; --l) {
         // layer l+2 (0-based mid index l): input act[l], pre-activation gradient dgrad[cur];
@@ -632,8 +557,9 @@ int cnn_backward(mvct_cnn_s *c, int n, cudaStream_t st)
         k_reduce_parts<<<(MID_SIZE + 31) / 32, 256, 0, st>>>(c->part, PB, MID_SIZE, MID_SIZE,
                                                             c->g + OFF_MID + l * MID_SIZE);
         // input gradient, masked by the previous activation (act[l])
-        k_conv32<1><<<tg, 256, 0, st>>>(c->dgrad[cur], c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l],
-                                        c->dgrad[cur ^ 1], H, W);
+        tc::k_conv32_tc<1><<<c->tc_grid, tc::THREADS, tc::SMEM_BYTES, st>>>(
+            c->dgrad[cur], c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l], c->dgrad[cur ^ 1], n, H, W,
+            c->tc_err);
         cur ^= 1;
     }
     // first layer: weight and bias gradient (W1 and b1 contiguous) from the scaled input
@@ -686,6 +612,8 @@ extern "C" int mvct_cnn_create(int32_t nmax, int32_t h, int32_t w, double scale,
     for (auto &d : c->dgrad) alloc((void **)&d, sizeof(__nv_bfloat16) * padpix * CH);
     alloc((void **)&c->part, sizeof(float) * (size_t)c->part_blocks * MID_SIZE);
     alloc((void **)&c->loss_part, sizeof(double) * c->num_sms * 8);
+    alloc((void **)&c->tc_err, sizeof(int));
+    c->tc_grid = c->num_sms * 4;
     ok = ok && cudaMallocHost((void **)&c->h_loss, sizeof(double) * c->num_sms * 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -701,6 +629,7 @@ extern "C" int mvct_cnn_create(int32_t nmax, int32_t h, int32_t w, double scale,
         if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(__nv_bfloat16) * padpix * CH);
     if (e == cudaSuccess) e = cudaMemset(c->m, 0, sizeof(float) * NPARAM);
     if (e == cudaSuccess) e = cudaMemset(c->v, 0, sizeof(float) * NPARAM);
+    if (e == cudaSuccess) e = cudaMemset(c->tc_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(c->w, params, sizeof(float) * NPARAM, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
         k_refresh<<<(NPARAM + 255) / 256, 256>>>(c->w, c->wf, c->wk_fwd, c->wk_bwd);
@@ -760,7 +689,13 @@ static int loss_and_grad(mvct_cnn_s *c, const float *d_in, const float *d_target
     int rc = cnn_backward(c, n, st);
     if (rc) return rc;
     CKC(cudaMemcpyAsync(c->h_loss, c->loss_part, sizeof(double) * gb, cudaMemcpyDeviceToHost, st));
+    int terr = 0;
+    CKC(cudaMemcpyAsync(&terr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKC(cudaStreamSynchronize(st));
+    if (terr) {
+        cudaMemsetAsync(c->tc_err, 0, sizeof(int), st);
+        return mvct_fail(MVCT_ETIMEOUT, "mvct_cnn: a tensor-core convolution gave up waiting for its MMAs");
+    }
     double s = 0.0;
     for (int b = 0; b < gb; ++b) s += c->h_loss[b];
     if (loss) *loss = s / (double)pix;

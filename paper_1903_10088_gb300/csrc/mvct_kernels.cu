@@ -80,7 +80,7 @@ k_weight_a1(const float *__restrict__ a1, const float *__restrict__ w, const flo
 __global__ void __launch_bounds__(kThreads)
 k_residual(Geo g, const float4 *__restrict__ rays, const int *__restrict__ ranges, const float *__restrict__ img,
            const float *__restrict__ imgT, const float *__restrict__ p, const float *__restrict__ w,
-           double *__restrict__ partials)
+           double *__restrict__ partials, float *__restrict__ e_out)
 {
     __shared__ double s[kWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -88,8 +88,10 @@ k_residual(Geo g, const float4 *__restrict__ rays, const int *__restrict__ range
     double acc = 0.0;
     for (int ray = blockIdx.x * kWarps + warp; ray < total; ray += gridDim.x * kWarps) {
         const float q = joseph_warp<true>(img, imgT, g.n, g.pc, __ldg(&rays[ray]), __ldg(ranges + ray), lane);
-        const double r = (double)q - (double)__ldg(p + ray);
-        acc += (double)__ldg(w + ray) * r * r;
+        const float pv = __ldg(p + ray), wv = __ldg(w + ray);
+        const double r = (double)q - (double)pv;
+        acc += (double)wv * r * r;
+        if (e_out && lane == 0) e_out[ray] = wv * (q - pv);
     }
     if (lane == 0) s[warp] = acc;
     __syncthreads();
@@ -265,9 +267,23 @@ cudaError_t launch_weight_a1(const mvct_plan_s *P, const float *w, const float *
 }
 
 cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float *imgT,
-                            const float *p, const float *w, double *partials, cudaStream_t st)
+                            const float *p, const float *w, double *partials, float *e_out, cudaStream_t st)
 {
-    k_residual<<<P->reduce_grid, kThreads, 0, st>>>(P->geo, P->rays, P->ray_range, img, imgT, p, w, partials);
+    k_residual<<<P->reduce_grid, kThreads, 0, st>>>(P->geo, P->rays, P->ray_range, img, imgT, p, w, partials,
+                                                    e_out);
+    return cudaGetLastError();
+}
+
+// y[k] += a * x[k], k < count.
+__global__ void k_axpy(float *__restrict__ y, const float *__restrict__ x, float a, size_t count)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += (size_t)gridDim.x * blockDim.x)
+        y[k] = fmaf(a, x[k], y[k]);
+}
+
+cudaError_t launch_axpy(const mvct_plan_s *P, float *y, const float *x, float a, size_t count, cudaStream_t st)
+{
+    k_axpy<<<P->reduce_grid, kThreads, 0, st>>>(y, x, a, count);
     return cudaGetLastError();
 }
 

@@ -179,7 +179,8 @@ cudaError_t launch_tv_grid(int n, const float *img, float eps, float *grad, doub
 cudaError_t launch_weight_a1(const mvct_plan_s *P, const float *w, const float *p, float *out, int *data_err,
                              cudaStream_t st);
 cudaError_t launch_residual(const mvct_plan_s *P, const float *img, const float *imgT,
-                            const float *p, const float *w, double *partials, cudaStream_t st);
+                            const float *p, const float *w, double *partials, float *e_out, cudaStream_t st);
+cudaError_t launch_axpy(const mvct_plan_s *P, float *y, const float *x, float a, size_t count, cudaStream_t st);
 cudaError_t launch_final_sum(const double *a, int na, double ca, const double *b, int nb, double cb,
                              double *out, cudaStream_t st);
 cudaError_t launch_setup_back(const mvct_plan_s *P, const float *wa1, float cb, float mu0,

@@ -124,7 +124,7 @@ class TuneReport(ctypes.Structure):
 
 
 EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvct_forward",
-           "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_recon", "mvct_last_error",
+           "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_objective_grad", "mvct_recon", "mvct_last_error",
            "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
            "mvct_batch_run", "mvct_batch_stats", "mvct_fbp", "mvct_cnn_param_count", "mvct_cnn_create",
            "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step", "mvct_plan_tune", "mvct_batch_tune",
@@ -145,6 +145,7 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     lib.mvct_back.argtypes = [vp, vp, vp, i32, vp]
     lib.mvct_tv_grad.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
     lib.mvct_objective.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp]
+    lib.mvct_objective_grad.argtypes = [vp, vp, vp, vp, ctypes.c_double, ctypes.c_double, vp, vp, vp]
     lib.mvct_recon.argtypes = [vp, vp, vp, ctypes.c_double, i32, ctypes.POINTER(ReconOpts), vp,
                                ctypes.POINTER(ReconStats), vp]
     lib.mvct_tv_grad_noalloc.argtypes = [vp, i32, ctypes.c_double, vp, vp, vp]
@@ -337,6 +338,18 @@ class Plan:
                                     _dev_f32(w, R, "w"), beta, eps, ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(_stream(stream))))
         return out
+
+    def objective_grad(self, img, p, w, beta: float, eps: float, out: Optional[torch.Tensor] = None,
+                       with_value: bool = False, stream=None):
+        """``mvct_objective_grad``: the gradient of Psi at img (and Psi if with_value)."""
+        out = torch.empty((self.n, self.n), device=img.device, dtype=torch.float32) if out is None else out
+        val = torch.zeros(1, device=img.device, dtype=torch.float64) if with_value else None
+        R = self.V * self.C
+        _check(lib().mvct_objective_grad(self._h, _dev_f32(img, self.n * self.n, "img"), _dev_f32(p, R, "p"),
+                                         _dev_f32(w, R, "w"), beta, eps, _dev_f32(out, self.n * self.n, "out"),
+                                         ctypes.c_void_p(val.data_ptr()) if val is not None else None,
+                                         ctypes.c_void_p(_stream(stream))))
+        return (out, val) if with_value else out
 
     def recon(self, p: torch.Tensor, w: torch.Tensor, beta: float, n_iter: int,
               img: Optional[torch.Tensor] = None, init_from_input: bool = False,

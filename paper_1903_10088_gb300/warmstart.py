@@ -52,6 +52,7 @@ class CNN:
         mvct._check(lib.mvct_cnn_create(batch_max, h, w, scale, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                         ctypes.byref(h_)))
         self._h, self.h, self.w, self.batch_max = h_, h, w, batch_max
+        self.scale = scale
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -276,6 +277,71 @@ def train(cnn: CNN, X, Y, epochs: int, batch: int, lr: float, seed: int = 0, log
     return hist
 
 
+def finetune_objective(cnn: CNN, seeds, device, steps: int, batch: int, lr: float, lr_final: Optional[float] = None,
+                       seed: int = 0, workers: int = 8, log=None):
+    """Fine-tune the network on the objective the loop minimises: Adam on
+    Psi(P(network(FBP))) of seeded training cases, Psi = 1/2 sum w (A mu - p)^2 +
+    beta TV_eps (Eq. 2 in its weighted-least-squares reading) and P the loop's
+    own constraints (mu >= 0, Eq. 1; 0 off the support the rays reach), with the
+    gradient dPsi/dmu from ``mvct_objective_grad`` (the plan's projector, matched
+    backprojection and TV kernels), zero where P clamps. The network's own backward pass takes that
+    gradient through ``mvct_cnn_train_step``: the step's mean-squared-error loss
+    (in the scaled domain, mean over M = batch*h*w pixels) against the target
+    out - g M / (2 s^2) has exactly g as its gradient with respect to the output.
+    Returns the mean Psi of the batches, per tenth of the steps."""
+    import math
+
+    torch = _torch()
+    from . import mvct
+
+    cases = make_cases(seeds, workers=workers)
+    g = cases[0].geom
+    N = len(cases)
+    plan = mvct.Plan(g, cases[0].n_subsets)
+    P = torch.stack([torch.from_numpy(c.p) for c in cases]).to(device)
+    W = torch.stack([torch.from_numpy(c.w) for c in cases]).to(device)
+    X = torch.empty((N, g.n, g.n), device=device)
+    for k in range(N):
+        plan.fbp(P[k], out=X[k])
+    # the support the rays reach: A^T 1 > 0
+    support = (plan.back(torch.ones((g.n_views, g.n_channels), device=device)) > 0).float()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    xb = torch.empty((batch, g.n, g.n), device=device)
+    out = torch.empty_like(xb)
+    grad = torch.empty_like(xb)
+    M = batch * g.n * g.n
+    c = M / (2.0 * cnn.scale * cnn.scale)
+    hist, acc, cnt = [], 0.0, 0
+    try:
+        for step in range(steps):
+            idx = rng.choice(N, size=batch, replace=False)
+            for k, i in enumerate(idx):
+                xb[k].copy_(X[int(i)])
+            cnn.forward(xb, out=out)
+            feasible = (out > 0).float() * support
+            proj = out * feasible
+            vals = []
+            for k, i in enumerate(idx):
+                _, v = plan.objective_grad(proj[k], P[int(i)], W[int(i)], cases[int(i)].beta, cases[int(i)].tv_eps,
+                                           out=grad[k], with_value=True)
+                vals.append(v)
+            target = out - c * grad * feasible
+            rate = lr
+            if lr_final is not None:
+                rate = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / max(1, steps - 1)))
+            cnn.train_step(xb, target, rate)
+            acc += float(torch.cat(vals).mean())
+            cnt += 1
+            if cnt == max(1, steps // 10) or step == steps - 1:
+                hist.append(acc / cnt)
+                if log:
+                    log(f"objective fine-tuning step {step + 1}/{steps}  mean Psi {hist[-1]:.4f}")
+                acc, cnt = 0.0, 0
+    finally:
+        plan.close()
+    return hist
+
+
 def infer(cnn: CNN, X, out=None, stream=None):
     """Warm-start images for the FBP images X ([N][n][n]), in chunks of the
     network's batch size."""
@@ -484,11 +550,22 @@ def _train_main(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     log = lambda s: print(s, file=sys.stderr, flush=True)
     t0 = time.perf_counter()
-    X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width,
-                          n_iter=args.target_iterations, workers=args.workers, log=log)
+    hist, tp = [], {}
+    init = load_weights(args.init) if args.init else init_params(args.seed)
+    if args.init and args.pair_epochs_skip:
+        cnn = CNN(args.batch, 512, 512, init)
+    else:
+        X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width,
+                              n_iter=args.target_iterations, workers=args.workers, log=log)
+        cnn = CNN(args.batch, X.shape[1], X.shape[2], init)
     t1 = time.perf_counter()
-    cnn = CNN(args.batch, X.shape[1], X.shape[2], init_params(args.seed))
-    hist = train(cnn, X, Y, args.epochs, args.batch, args.lr, args.seed, log, lr_final=args.lr_final)
+    if not (args.init and args.pair_epochs_skip):
+        hist = train(cnn, X, Y, args.epochs, args.batch, args.lr, args.seed, log, lr_final=args.lr_final)
+        del X, Y
+    psi_hist = []
+    if args.psi_steps > 0:
+        psi_hist = finetune_objective(cnn, range(TRAIN_SEED0, TRAIN_SEED0 + args.psi_cases), dev, args.psi_steps,
+                                      args.batch, args.psi_lr, args.psi_lr_final, args.seed, args.workers, log)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     params = cnn.params()
@@ -498,7 +575,10 @@ def _train_main(args):
     rec = dict(pairs=args.pairs, train_seeds=[TRAIN_SEED0, TRAIN_SEED0 + args.pairs - 1], epochs=args.epochs,
                batch=args.batch, lr=args.lr, lr_final=args.lr_final, seed=args.seed,
                target_iterations=args.target_iterations, target_options="the library defaults",
-               epoch_loss=hist, pair_generation_s=t1 - t0, pair_timing=tp, training_s=t2 - t1,
+               init=os.path.basename(args.init) if args.init else None, epoch_loss=hist,
+               objective_finetune=dict(steps=args.psi_steps, lr=args.psi_lr, lr_final=args.psi_lr_final,
+                                       cases=args.psi_cases, mean_psi=psi_hist) if args.psi_steps else None,
+               pair_generation_s=t1 - t0, pair_timing=tp, training_s=t2 - t1,
                steps=args.epochs * (args.pairs // args.batch))
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
         json.dump(rec, f, indent=1)
@@ -559,6 +639,13 @@ def _main(argv=None):
         ap.add_argument("--lr-final", type=float, default=None, help="cosine decay of the step size to this value")
         ap.add_argument("--seed", type=int, default=0)
         ap.add_argument("--target-iterations", type=int, default=N_ITER_TARGET)
+        ap.add_argument("--init", default=None, help="start from these weights instead of a fresh network")
+        ap.add_argument("--pair-epochs-skip", action="store_true",
+                        help="with --init: no pair training, only the objective fine-tuning")
+        ap.add_argument("--psi-steps", type=int, default=0, help="objective fine-tuning steps after the pairs")
+        ap.add_argument("--psi-lr", type=float, default=1e-4)
+        ap.add_argument("--psi-lr-final", type=float, default=1e-5)
+        ap.add_argument("--psi-cases", type=int, default=1000, help="training cases of the fine-tuning")
         ap.add_argument("--out", default=weights_path())
         return _train_main(ap.parse_args(argv))
     ap.add_argument("--weights", default=None)

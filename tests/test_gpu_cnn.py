@@ -1,7 +1,9 @@
 """The warm-start network's GPU kernels (BF16 tensor-core convolutions, FP32
 accumulation) against the FP64 CPU reference that rounds at the same points:
-forward output, loss, and the full parameter gradient; determinism; and that
-Adam steps lower the loss."""
+forward output, loss, and the full parameter gradient (small ragged images, a
+row width that leaves a partial 128-pixel tile, and a full-size 2 x 512^2
+batch, so the weight-gradient reduction runs over whole images); determinism;
+and that Adam steps lower the loss."""
 import numpy as np
 import pytest
 import torch
@@ -41,7 +43,7 @@ def data(shape, seed):
     return x, y
 
 
-@pytest.mark.parametrize("shape", [(2, 24, 32), (1, 19, 37), (3, 8, 16)])
+@pytest.mark.parametrize("shape", [(2, 24, 32), (1, 19, 37), (3, 8, 16), (2, 512, 512), (1, 130, 257)])
 def test_forward_matches_reference(mvct, shape):
     p = params_for_test(1)
     x, _ = data(shape, 2)
@@ -55,7 +57,7 @@ def test_forward_matches_reference(mvct, shape):
     net.close()
 
 
-@pytest.mark.parametrize("shape", [(2, 24, 32), (1, 19, 37)])
+@pytest.mark.parametrize("shape", [(2, 24, 32), (1, 19, 37), (2, 512, 512)])
 def test_gradient_matches_reference(mvct, shape):
     p = params_for_test(3)
     x, y = data(shape, 4)
