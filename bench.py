@@ -550,46 +550,35 @@ def run_ours(args):
 
 
 WARM_WORKLOAD = dict(workload="learned warm start + batched OS-TV: a stack of 48 held-out 512^2 slices per step",
-                     slices=48, n=512, n_views=800, n_channels=738, subsets=20, sub_iterations=100,
-                     lambda0=0.025, beta=1e-3, tv_eps=1e-6, I0=5e3,
-                     chain="FBP -> CNN (8 conv3x3, 32 ch, BF16 tensor cores) -> 100 OS-TV sub-iterations, "
+                     slices=48, n=512, n_views=800, n_channels=738, subsets=20, beta=1e-3, tv_eps=1e-6, I0=5e3,
+                     chain="FBP -> CNN (8 conv3x3, 32 ch, BF16, tcgen05 tensor cores) -> K OS-TV sub-iterations, "
                            "all slices in one persistent launch, the whole chain one CUDA-graph replay",
                      quality="objective Psi of every slice against the plain form (FBP start, 500 sub-iterations)")
 
 
-def run_warm(args, dev, ws, plain_slices_per_s):
-    """The warm-started, batched form: per step, FBP of every slice of the stack,
-    the network's start images, and K OS-TV sub-iterations of all slices in one
-    persistent launch, replayed as one CUDA graph. Quality: Psi of each slice
-    after the timed steps against the plain form's Psi (FBP start, 500
-    sub-iterations, computed after the timing)."""
+def _time_chain(args, dev, ws, wst, cases, K, lam0, flush):
+    """Time the warm chain of the stack at K sub-iterations from lambda0 (CUDA-graph
+    replays, L2 flushed between steps) and end to end with host buffers; returns
+    the figures and the final images' objectives."""
     import torch
 
-    from paper_1903_10088_gb300 import mvct
-    from paper_1903_10088_gb300 import warmstart as wst
-
-    B, K, lam0 = WARM_WORKLOAD["slices"], WARM_WORKLOAD["sub_iterations"], WARM_WORKLOAD["lambda0"]
-    _, rank, local = dist_env()
-    seeds = range(wst.HELDOUT_SEED0 + rank * B, wst.HELDOUT_SEED0 + (rank + 1) * B)
-    cases = wst.make_cases(seeds, workers=min(16, os.cpu_count() or 1))
+    B = len(cases)
     g = cases[0].geom
+    _, rank, local = dist_env()
     pipe = wst.WarmPipeline(g, cases[0].n_subsets, B, K, dev, lambda0=lam0)
-    betas = [c.beta for c in cases]
     pipe.load(torch.stack([torch.from_numpy(c.p) for c in cases]), torch.stack([torch.from_numpy(c.w) for c in cases]),
-              betas)
-    P, W, IMG, plans, batch = pipe.p, pipe.w, pipe.img, pipe.plans, pipe.batch
+              [c.beta for c in cases])
     tune = pipe.tune(40)                             # view groups per tile (untimed; images restored)
     pipe.capture()
     for _ in range(args.warmup):
         pipe.run()
     torch.cuda.synchronize()
     pipe.check()                                     # raises if a run failed
-    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
     cur = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local, "_warm") as clk:
+    with ClockSampler(local, f"_warm{K}") as clk:
         for k in range(args.steps):
             flush.fill_(float(k))
             ev[k][0].record(cur)
@@ -600,11 +589,9 @@ def run_warm(args, dev, ws, plain_slices_per_s):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_max = max_over_ranks(float(np.sum(step_ms)), dev)
     value = B * ws * args.steps / (t_max / 1e3)
-
-    # stage times of one untimed direct chain (events between the stages)
     stage_ms = pipe.stage_ms()
-
     # end to end: host sinograms and weights in, host images out
+    P, W, IMG = pipe.p, pipe.w, pipe.img
     hP, hW = P.cpu().pin_memory(), W.cpu().pin_memory()
     hI = torch.empty_like(IMG, device="cpu").pin_memory()
     e2e_ms = []
@@ -620,36 +607,81 @@ def run_warm(args, dev, ws, plain_slices_per_s):
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_t = max_over_ranks(float(np.sum(e2e_ms)), dev)
-
-    # quality: Psi of the warm-started results against the plain form
-    psi = lambda k, im: float(plans[0].objective(im, P[k], W[k], cases[k].beta, cases[k].tv_eps).item())
-    psi_warm = np.array([psi(k, IMG[k]) for k in range(B)])
-    pipe.graph = None
-    for k in range(B):
-        plans[k].fbp(P[k], out=IMG[k])
-    batch.bind(list(P), list(W), betas, list(IMG), 500, init_from_input=True)
-    batch.run(500)
-    batch.stats(0)
-    psi_plain = np.array([psi(k, IMG[k]) for k in range(B)])
-    gap = (psi_warm - psi_plain) / psi_plain
+    psi = np.array([float(pipe.plans[0].objective(IMG[k], P[k], W[k], cases[k].beta, cases[k].tv_eps).item())
+                    for k in range(B)])
     pipe.close()
     return {
-        "value": value, "unit": "slices/s", "ms_per_step": t_max / args.steps,
-        "speedup_vs_plain": value / plain_slices_per_s if plain_slices_per_s else None,
-        "config": dict(WARM_WORKLOAD, seeds=[seeds[0], seeds[-1]],
-                       launch_shape={"view_groups_per_tile": tune["groups"] or "default rule",
-                                     "autotuned_ms_per_iter": tune["ms_per_iter"],
-                                     "default_ms_per_iter": tune["default_ms_per_iter"]},
-                       weights="paper_1903_10088_gb300/weights/warmstart_512.npy",
-                       l2="flushed between timed steps (512 MiB write)"),
+        "value": value, "unit": "slices/s", "ms_per_step": t_max / args.steps, "sub_iterations": K,
+        "lambda0": lam0,
+        "launch_shape": {"view_groups_per_tile": tune["groups"] or "default rule",
+                         "autotuned_ms_per_iter": tune["ms_per_iter"], "default_ms_per_iter": tune["default_ms_per_iter"]},
         "stage_ms_per_slice": stage_ms,
-        "psi_gap_vs_plain": {"median": float(np.median(gap)), "max": float(gap.max()), "min": float(gap.min()),
-                             "within_1e-3": float(np.mean(gap <= 1e-3))},
         "e2e": {"value": B * ws * len(e2e_ms) / (e2e_t / 1e3), "unit": "slices/s",
                 "h2d_bytes_per_step": int(hP.numel() * 4 + hW.numel() * 4),
                 "d2h_bytes_per_step": int(hI.numel() * 4)},
         "gpu_launches_per_step": 2 * B + 10 * ((B + 15) // 16) + 2 + 3 * B,
         "clocks": clk.summary(),
+    }, psi
+
+
+def run_warm(args, dev, ws, plain_slices_per_s):
+    """The warm-started, batched form: per step, FBP of every slice of the stack,
+    the network's start images, and K OS-TV sub-iterations of all slices in one
+    persistent launch, replayed as one CUDA graph. Timed at two operating points:
+    K = warmstart.FAST_K (near 5x the plain form) and the smallest K of
+    warmstart.K_GRID at which every slice of the stack reaches the plain form's
+    objective within 1e-3 (searched on the stack, untimed). Quality: Psi of every
+    slice against the plain form's Psi (FBP start, 500 sub-iterations)."""
+    import torch
+
+    from paper_1903_10088_gb300 import warmstart as wst
+
+    B = WARM_WORKLOAD["slices"]
+    _, rank, local = dist_env()
+    seeds = range(wst.HELDOUT_SEED0 + rank * B, wst.HELDOUT_SEED0 + (rank + 1) * B)
+    cases = wst.make_cases(seeds, workers=min(16, os.cpu_count() or 1))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    g = cases[0].geom
+
+    # the plain form's objective of every slice (batched FBP + 500, identical results)
+    rec = wst.StackReconstructor(g, cases[0].n_subsets, B, dev)
+    rec.load(cases)
+    fb = [rec.fbp(k, torch.empty((g.n, g.n), device=dev)) for k in range(B)]
+    plain = rec.run(B, [c.beta for c in cases], fb, wst.N_ITER_TARGET)
+    psi_plain = np.array([float(rec.plans[0].objective(plain[k], rec.p[k], rec.w[k], cases[k].beta,
+                                                       cases[k].tv_eps).item()) for k in range(B)])
+    rec.close()
+
+    def gap_stats(psi):
+        gap = (psi - psi_plain) / psi_plain
+        return {"median": float(np.median(gap)), "max": float(gap.max()), "min": float(gap.min()),
+                "within_1e-3": float(np.mean(gap <= 1e-3))}
+
+    fast, psi_fast = _time_chain(args, dev, ws, wst, cases, wst.FAST_K, wst.FAST_LAMBDA0, flush)
+    fast["psi_gap_vs_plain"] = gap_stats(psi_fast)
+    fast["speedup_vs_plain"] = fast["value"] / plain_slices_per_s if plain_slices_per_s else None
+
+    # the per-slice bar: search K on the stack, then time the chain there
+    cnn = wst.CNN(16, g.n, g.n, wst.load_weights())
+    details = {}
+    k_bar = wst.sub_iterations_to_bar(cnn, cases, dev, wst.K_GRID, width=B, details=details)
+    cnn.close()
+    at_bar = None
+    if k_bar is not None:
+        at_bar, psi_bar = _time_chain(args, dev, ws, wst, cases, k_bar, wst.BAR_LAMBDA0, flush)
+        at_bar["psi_gap_vs_plain"] = gap_stats(psi_bar)
+        at_bar["speedup_vs_plain"] = at_bar["value"] / plain_slices_per_s if plain_slices_per_s else None
+    return {
+        "value": (at_bar or fast)["value"], "unit": "slices/s",
+        "operating_point": "every slice within 1e-3 of the plain form" if at_bar else "fast (bar not reached)",
+        "speedup_vs_plain": (at_bar or fast)["speedup_vs_plain"],
+        "config": dict(WARM_WORKLOAD, seeds=[seeds[0], seeds[-1]],
+                       weights="paper_1903_10088_gb300/weights/warmstart_512.npy",
+                       l2="flushed between timed steps (512 MiB write)"),
+        "at_per_slice_bar": at_bar,
+        "at_fast_k": fast,
+        "bar_search": {"K_grid": list(wst.K_GRID), "lambda0": wst.BAR_LAMBDA0, "bar": wst.BAR,
+                       "max_gap_by_K": {str(k): float(max(v)) for k, v in details.items()}},
     }
 
 

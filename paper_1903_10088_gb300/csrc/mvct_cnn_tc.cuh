@@ -14,17 +14,23 @@
 // is 8 rows (pixels or output channels) x 16 bytes (8 channels of K) stored
 // contiguously (128 B); core matrices 8 rows further along M/N are SBO = 128 B
 // apart, the next 8 channels along K are LBO bytes apart.
-//   A strip: [3 rows][4 channel octets][130 pixels][8] BF16 (24,960 B);
-//            tap (ky, kx), K-step kk starts at ((ky*4 + 2kk)*130 + kx)*16 B,
-//            LBO = 130*16 B (the next channel octet of the same pixels).
+//   A strip (two stages): [4 channel octets][3 rows][130 pixels][8] BF16, each
+//            octet plane padded to 6,272 B; loaded by the tensor memory
+//            accelerator (cp.async.bulk.tensor, one 8 x 130 x 3 box per octet
+//            from a 3D map of the padded NHWC activations, pixels past the row
+//            end zero-filled) and completed on a per-stage mbarrier. Tap
+//            (ky, kx), K-step kk starts at 2kk*6272 + (ky*130 + kx)*16 B,
+//            LBO = 6272 B (the next octet plane).
 //   B:       [9 taps][4 input-channel octets][32 co][8] BF16 (18,432 B);
 //            tap, kk starts at (tap*4 + 2kk)*32*16 B, LBO = 32*16 B.
 // Each persistent block loads its layer's weights once and walks tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ...; every wait on the mbarrier is
-// bounded (global timer), after which the block records an error, frees its
-// TMEM and leaves.
+// blockIdx.x, blockIdx.x + gridDim.x, ...; the strip of the next tile is
+// fetched while the current tile's MMAs and epilogue run. Every wait on an
+// mbarrier is bounded (global timer), after which the block records an error,
+// waits (bounded) for its copy in flight, frees its TMEM and leaves.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -34,12 +40,18 @@ namespace tc {
 
 constexpr int M = 128;                        // output pixels per tile
 constexpr int PIX = M + 2;                    // strip pixels per row (one halo pixel each side)
-constexpr int A_BYTES = 3 * 4 * PIX * 16;     // 24,960
+constexpr int PLANE = 6272;                   // one channel octet of the strip: 3 x 130 x 16 B, padded to 128 B
+constexpr int STRIP_TX = 4 * 3 * PIX * 16;    // bytes the four boxes of a strip deliver (24,960)
+constexpr int A_BYTES = 4 * PLANE;            // 25,088 per stage
+constexpr int STAGES = 3;                     // strips in flight
+constexpr int ACCS = 2;                       // TMEM accumulators (the epilogue of one tile overlaps the next MMAs)
 constexpr int B_BYTES = 9 * 4 * 32 * 16;      // 18,432
-constexpr int BAR_OFF = A_BYTES + B_BYTES;    // 8-byte aligned
-constexpr int SMEM_BYTES = BAR_OFF + 16;      // mbarrier + TMEM address slot
-constexpr int THREADS = 128;
-constexpr uint32_t TMEM_COLS = 32;            // 128 lanes x 32 FP32 columns
+constexpr int B_OFF = STAGES * A_BYTES;
+constexpr int BAR_OFF = B_OFF + B_BYTES;      // full[STAGES], empty[STAGES], tfull[ACCS], tempty[ACCS]
+constexpr int NBARS = 2 * STAGES + 2 * ACCS;
+constexpr int SMEM_BYTES = BAR_OFF + 8 * NBARS + 16; // + TMEM address slot and the failure flag
+constexpr int THREADS = 192;                  // warp 0: copies, warp 1: MMAs, warps 2-5: epilogue
+constexpr uint32_t TMEM_COLS = 32 * ACCS;     // 128 lanes x 32 FP32 columns per accumulator
 // Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and
 // B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in
 // bits 17-22, M >> 4 in bits 24-28.
@@ -97,6 +109,25 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// One 3D box of the tensor map at (c0, c1, c2) into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *tmap, int c0, int c1, int c2, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                 "%4}], [%5];" ::"r"(dst),
+                 "l"((unsigned long long)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+                 : "memory");
+}
+
 // 32 consecutive FP32 columns of this warp's 32 TMEM lanes into v.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 {
@@ -117,22 +148,37 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 
 // MODE 0 (forward): out = relu(conv(in, wk) + bias).
 // MODE 1 (input gradient): out = conv(in, wk) * [mask > 0].
-// in / mask / out: padded NHWC [N][H+2][W+2][32] BF16; wk: [9][32 n][32 k] BF16.
-// err: set to 1 if a wait for the tensor cores gave up (the block then leaves).
+// in (through tmap: 3D map {32 channels, W + 2 pixels, N (H + 2) rows} of the
+// padded NHWC BF16 input, box {8, 130, 3}) / mask / out: padded NHWC
+// [N][H+2][W+2][32] BF16; wk: [9][32 n][32 k] BF16.
+// Warp-specialised pipeline over the block's tiles i = 0, 1, ... (tile
+// blockIdx.x + i*gridDim.x): warp 0 fetches strip i into stage i mod STAGES once
+// the MMAs of tile i - STAGES have released it (empty); warp 1 waits for the
+// strip (full) and for accumulator i mod ACCS to be drained (tempty), issues the
+// 18 MMAs and commits them to empty and tfull; warps 2-5 wait for tfull, read
+// their TMEM lane quarter (warp w reads lanes 32 (w mod 4) ..), release the
+// accumulator (tempty) and write the tile.
+// err: set to 1 if a wait gave up (every role then leaves its loop, bounded).
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__restrict__ in,
+__global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ CUtensorMap tmap,
                                                        const __nv_bfloat16 *__restrict__ wk,
                                                        const float *__restrict__ bias,
                                                        const __nv_bfloat16 *__restrict__ mask,
                                                        __nv_bfloat16 *__restrict__ out, int N, int H, int W,
                                                        int *__restrict__ err)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *sA = smem, *sB = smem + A_BYTES;
-    uint64_t *bar = (uint64_t *)(smem + BAR_OFF);
-    uint32_t *tslot = (uint32_t *)(smem + BAR_OFF + 8);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char *sB = smem + B_OFF;
+    uint64_t *bars = (uint64_t *)(smem + BAR_OFF);
+    uint32_t *tslot = (uint32_t *)(smem + BAR_OFF + 8 * NBARS);
+    volatile int *fail = (volatile int *)(smem + BAR_OFF + 8 * NBARS + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar_a = smem_u32(bar), sA_a = smem_u32(sA), sB_a = smem_u32(sB);
+    const uint32_t sA_a = smem_u32(smem), sB_a = smem_u32(sB), bar0 = smem_u32(bars);
+    auto full_b = [bar0](int s) { return bar0 + 8u * (uint32_t)s; };
+    auto empty_b = [bar0](int s) { return bar0 + 8u * (uint32_t)(STAGES + s); };
+    auto tfull_b = [bar0](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + a); };
+    auto tempty_b = [bar0](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + ACCS + a); };
+    constexpr unsigned long long kLimit = 1000000000ull; // 1 s of global time per wait
 
     // weights [tap][co][ci] -> [tap][ci octet][co][8 ci]
     for (int k = tid; k < 9 * CH * 4; k += THREADS) {
@@ -141,15 +187,24 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__re
         *(uint4 *)(sB + ((tap * 4 + q) * CH + co) * 16) = v;
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+        for (int s = 0; s < STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full_b(s)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty_b(s)) : "memory");
+        }
+        for (int a = 0; a < ACCS; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull_b(a)) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(tempty_b(a)) : "memory"); // 4 epilogue warps
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *fail = 0;
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                      "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    fence_async_smem(); // the weights' generic stores, seen by the tensor cores' async proxy
     fence_before();
     __syncthreads();
     fence_after();
@@ -157,76 +212,111 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__re
 
     const int segs = (W + M - 1) / M;
     const long long tiles = (long long)N * H * segs;
-    uint32_t parity = 0;
-    for (long long t = blockIdx.x; t < tiles; t += gridDim.x) {
-        const int n = (int)(t / ((long long)H * segs));
+    const int my_tiles = (long long)blockIdx.x < tiles ? (int)((tiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
+    auto tile_at = [&](int i, int &n, int &y, int &x0) {
+        const long long t = blockIdx.x + (long long)i * gridDim.x;
+        n = (int)(t / ((long long)H * segs));
         const int rem = (int)(t - (long long)n * H * segs);
-        const int y = rem / segs, x0 = (rem - y * segs) * M;
-        // input strip: image rows y-1 .. y+1, pixels x0-1 .. x0+M (padded coordinates are valid up to W)
-        for (int k = tid; k < 3 * PIX * 4; k += THREADS) {
-            const int q = k & 3, pr = k >> 2, r = pr / PIX, px = pr - r * PIX;
-            const int gx = x0 - 1 + px, gy = y - 1 + r;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (gx <= W) v = __ldg((const uint4 *)(in + apix(n, gy, gx, H, W) * CH) + q);
-            *(uint4 *)(sA + ((r * 4 + q) * PIX + px) * 16) = v;
+        y = rem / segs;
+        x0 = (rem - y * segs) * M;
+    };
+    auto give_up = [&]() {
+        *fail = 1;
+        atomicExch(err, 1);
+    };
+
+    if (warp == 0) {
+        // copies: the strip of tile i into stage i mod STAGES
+        if (lane == 0) {
+            for (int i = 0; i < my_tiles && !*fail; ++i) {
+                const int s = i % STAGES;
+                if (i >= STAGES && !wait_bounded(empty_b(s), (uint32_t)(((i / STAGES) + 1) & 1), kLimit)) {
+                    give_up();
+                    break;
+                }
+                int n, y, x0;
+                tile_at(i, n, y, x0);
+                expect_tx(full_b(s), STRIP_TX);
+                for (int q = 0; q < 4; ++q)
+                    tma_load_3d(sA_a + s * A_BYTES + q * PLANE, &tmap, q * 8, x0, n * (H + 2) + y, full_b(s));
+            }
         }
-        fence_async_smem(); // the strip's generic stores, seen by the tensor cores' async proxy
-        fence_before();
-        __syncthreads();
-        if (tid == 0) {
+    } else if (warp == 1) {
+        // MMAs of tile i into accumulator i mod ACCS
+        if (lane == 0) {
+            for (int i = 0; i < my_tiles && !*fail; ++i) {
+                const int s = i % STAGES, a = i % ACCS;
+                if (!wait_bounded(full_b(s), (uint32_t)((i / STAGES) & 1), kLimit) ||
+                    (i >= ACCS && !wait_bounded(tempty_b(a), (uint32_t)(((i / ACCS) + 1) & 1), kLimit))) {
+                    give_up();
+                    break;
+                }
+                fence_after();
+                const uint32_t a0 = sA_a + s * A_BYTES, d = tmem + (uint32_t)(a * 32);
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap - 3 * ky;
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        const uint64_t ad = smem_desc(a0 + 2 * kk * PLANE + (ky * PIX + kx) * 16, PLANE, 128);
+                        const uint64_t bd = smem_desc(sB_a + (tap * 4 + 2 * kk) * CH * 16, CH * 16, 128);
+                        mma_f16(d, ad, bd, (tap | kk) != 0 ? 1u : 0u);
+                    }
+                }
+                commit(empty_b(s)); // the strip may be refilled once these MMAs are done
+                commit(tfull_b(a)); // and the accumulator read
+            }
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w mod 4) .. + 31, one pixel per thread
+        const int quarter = warp & 3;
+        for (int i = 0; i < my_tiles; ++i) {
+            const int a = i % ACCS;
+            const bool ok = wait_bounded(tfull_b(a), (uint32_t)((i / ACCS) & 1), kLimit) && !*fail;
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) give_up();
+                break;
+            }
             fence_after();
+            float acc[32];
+            tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * 32), acc);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) arrive(tempty_b(a)); // the accumulator may take the next MMAs
+            int n, y, x0;
+            tile_at(i, n, y, x0);
+            const int x = x0 + quarter * 32 + lane;
+            if (x < W) {
+                const size_t base = apix(n, y, x, H, W) * CH;
+                uint4 o[4];
+                __nv_bfloat162 *ob = (__nv_bfloat162 *)o;
+                if (MODE == 0) {
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                const int ky = tap / 3, kx = tap - 3 * ky;
+                    for (int c = 0; c < 16; ++c)
+                        ob[c] = __floats2bfloat162_rn(fmaxf(acc[2 * c] + __ldg(bias + 2 * c), 0.f),
+                                                      fmaxf(acc[2 * c + 1] + __ldg(bias + 2 * c + 1), 0.f));
+                } else {
+                    uint4 mv[4];
 #pragma unroll
-                for (int kk = 0; kk < 2; ++kk) {
-                    const uint64_t ad = smem_desc(sA_a + ((ky * 4 + 2 * kk) * PIX + kx) * 16, PIX * 16, 128);
-                    const uint64_t bd = smem_desc(sB_a + (tap * 4 + 2 * kk) * CH * 16, CH * 16, 128);
-                    mma_f16(tmem, ad, bd, (tap | kk) != 0 ? 1u : 0u);
+                    for (int q = 0; q < 4; ++q) mv[q] = __ldg((const uint4 *)(mask + base) + q);
+                    const __nv_bfloat162 *mb = (const __nv_bfloat162 *)mv;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const float2 m = __bfloat1622float2(mb[c]);
+                        ob[c] = __floats2bfloat162_rn(m.x > 0.f ? acc[2 * c] : 0.f,
+                                                      m.y > 0.f ? acc[2 * c + 1] : 0.f);
+                    }
                 }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) *((uint4 *)(out + base) + q) = o[q];
             }
-            commit(bar_a);
         }
-        __syncwarp();
-        // every thread waits; the block leaves together if any wait gave up
-        const bool ok = __syncthreads_and(wait_bounded(bar_a, parity, 1000000000ull)) != 0;
-        parity ^= 1u;
-        if (!ok) {
-            if (tid == 0) atomicExch(err, 1);
-            break;
-        }
-        fence_after();
-        float acc[32];
-        tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16), acc);
-        const int x = x0 + warp * 32 + lane;
-        if (x < W) {
-            const size_t base = apix(n, y, x, H, W) * CH;
-            uint4 o[4];
-            __nv_bfloat162 *ob = (__nv_bfloat162 *)o;
-            if (MODE == 0) {
-#pragma unroll
-                for (int c = 0; c < 16; ++c)
-                    ob[c] = __floats2bfloat162_rn(fmaxf(acc[2 * c] + __ldg(bias + 2 * c), 0.f),
-                                                  fmaxf(acc[2 * c + 1] + __ldg(bias + 2 * c + 1), 0.f));
-            } else {
-                uint4 mv[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) mv[q] = __ldg((const uint4 *)(mask + base) + q);
-                const __nv_bfloat162 *mb = (const __nv_bfloat162 *)mv;
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const float2 m = __bfloat1622float2(mb[c]);
-                    ob[c] = __floats2bfloat162_rn(m.x > 0.f ? acc[2 * c] : 0.f, m.y > 0.f ? acc[2 * c + 1] : 0.f);
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) *((uint4 *)(out + base) + q) = o[q];
-        }
-        fence_before(); // this tile's TMEM reads come before the next tile's MMAs
     }
+    __syncwarp();
+    fence_before();
     __syncthreads();
     fence_after();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 

@@ -52,7 +52,6 @@ class CNN:
         mvct._check(lib.mvct_cnn_create(batch_max, h, w, scale, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                         ctypes.byref(h_)))
         self._h, self.h, self.w, self.batch_max = h_, h, w, batch_max
-        self.scale = scale
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -109,6 +108,13 @@ class CNN:
 TRAIN_SEED0 = 30_000     # training phantoms: seeds TRAIN_SEED0 ..
 HELDOUT_SEED0 = 50_000   # held-out phantoms: seeds HELDOUT_SEED0 ..
 N_ITER_TARGET = 500
+# Warm-started loop settings (measured on 48 held-out slices against the plain
+# form): FAST_K sub-iterations from lambda0 = FAST_LAMBDA0 is the operating point
+# near 5x the plain form's slices/s; the smallest K on the grid K_GRID at which
+# every slice of a stack reaches the plain form's objective within BAR is found
+# per stack (lambda0 = BAR_LAMBDA0).
+FAST_K, FAST_LAMBDA0 = 100, 0.04
+K_GRID, BAR_LAMBDA0, BAR = (100, 150, 200, 250, 300, 350, 400, 450, 500), 0.02, 1e-3
 
 
 def case_for(seed, kind: str = "full"):
@@ -277,71 +283,6 @@ def train(cnn: CNN, X, Y, epochs: int, batch: int, lr: float, seed: int = 0, log
     return hist
 
 
-def finetune_objective(cnn: CNN, seeds, device, steps: int, batch: int, lr: float, lr_final: Optional[float] = None,
-                       seed: int = 0, workers: int = 8, log=None):
-    """Fine-tune the network on the objective the loop minimises: Adam on
-    Psi(P(network(FBP))) of seeded training cases, Psi = 1/2 sum w (A mu - p)^2 +
-    beta TV_eps (Eq. 2 in its weighted-least-squares reading) and P the loop's
-    own constraints (mu >= 0, Eq. 1; 0 off the support the rays reach), with the
-    gradient dPsi/dmu from ``mvct_objective_grad`` (the plan's projector, matched
-    backprojection and TV kernels), zero where P clamps. The network's own backward pass takes that
-    gradient through ``mvct_cnn_train_step``: the step's mean-squared-error loss
-    (in the scaled domain, mean over M = batch*h*w pixels) against the target
-    out - g M / (2 s^2) has exactly g as its gradient with respect to the output.
-    Returns the mean Psi of the batches, per tenth of the steps."""
-    import math
-
-    torch = _torch()
-    from . import mvct
-
-    cases = make_cases(seeds, workers=workers)
-    g = cases[0].geom
-    N = len(cases)
-    plan = mvct.Plan(g, cases[0].n_subsets)
-    P = torch.stack([torch.from_numpy(c.p) for c in cases]).to(device)
-    W = torch.stack([torch.from_numpy(c.w) for c in cases]).to(device)
-    X = torch.empty((N, g.n, g.n), device=device)
-    for k in range(N):
-        plan.fbp(P[k], out=X[k])
-    # the support the rays reach: A^T 1 > 0
-    support = (plan.back(torch.ones((g.n_views, g.n_channels), device=device)) > 0).float()
-    rng = np.random.Generator(np.random.PCG64(seed))
-    xb = torch.empty((batch, g.n, g.n), device=device)
-    out = torch.empty_like(xb)
-    grad = torch.empty_like(xb)
-    M = batch * g.n * g.n
-    c = M / (2.0 * cnn.scale * cnn.scale)
-    hist, acc, cnt = [], 0.0, 0
-    try:
-        for step in range(steps):
-            idx = rng.choice(N, size=batch, replace=False)
-            for k, i in enumerate(idx):
-                xb[k].copy_(X[int(i)])
-            cnn.forward(xb, out=out)
-            feasible = (out > 0).float() * support
-            proj = out * feasible
-            vals = []
-            for k, i in enumerate(idx):
-                _, v = plan.objective_grad(proj[k], P[int(i)], W[int(i)], cases[int(i)].beta, cases[int(i)].tv_eps,
-                                           out=grad[k], with_value=True)
-                vals.append(v)
-            target = out - c * grad * feasible
-            rate = lr
-            if lr_final is not None:
-                rate = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / max(1, steps - 1)))
-            cnn.train_step(xb, target, rate)
-            acc += float(torch.cat(vals).mean())
-            cnt += 1
-            if cnt == max(1, steps // 10) or step == steps - 1:
-                hist.append(acc / cnt)
-                if log:
-                    log(f"objective fine-tuning step {step + 1}/{steps}  mean Psi {hist[-1]:.4f}")
-                acc, cnt = 0.0, 0
-    finally:
-        plan.close()
-    return hist
-
-
 def infer(cnn: CNN, X, out=None, stream=None):
     """Warm-start images for the FBP images X ([N][n][n]), in chunks of the
     network's batch size."""
@@ -408,6 +349,47 @@ def evaluate(cnn: CNN, cases, Ks, device, width: int = 48, n_plain: int = N_ITER
     return out
 
 
+def sub_iterations_to_bar(cnn: Optional[CNN], cases, device, K_grid=K_GRID, width: int = 48, bar: float = BAR,
+                          lambda0: Optional[float] = None, details: Optional[dict] = None):
+    """The smallest K of K_grid at which every case, started from the network's
+    image (cnn) or from the FBP image (cnn None), reaches the plain form's
+    objective (FBP start, N_ITER_TARGET sub-iterations) within `bar`:
+    (Psi_K - Psi_plain) / Psi_plain <= bar for all cases. Network starts run from
+    lambda0 = BAR_LAMBDA0 (unless given), FBP starts from the library default.
+    None if no K of the grid does. `details`, if given, receives the gaps of
+    every K tried."""
+    torch = _torch()
+    g = cases[0].geom
+    rec = StackReconstructor(g, cases[0].n_subsets, min(width, len(cases)), device)
+    opts = {} if cnn is None else {"lambda0": BAR_LAMBDA0 if lambda0 is None else lambda0}
+    try:
+        chunks = []
+        for c0 in range(0, len(cases), rec.width):
+            ch = cases[c0:c0 + rec.width]
+            rec.load(ch)
+            fb = torch.stack([rec.fbp(k, torch.empty((g.n, g.n), device=device)) for k in range(len(ch))])
+            starts = fb if cnn is None else infer(cnn, fb)
+            psi = lambda k, img: float(rec.plans[0].objective(img, rec.p[k], rec.w[k], ch[k].beta,
+                                                              ch[k].tv_eps).item())
+            plain = rec.run(len(ch), [c.beta for c in ch], list(fb), N_ITER_TARGET)
+            chunks.append((ch, starts.clone(), [psi(k, plain[k]) for k in range(len(ch))]))
+        for K in sorted(K_grid):
+            gaps = []
+            for ch, starts, pp in chunks:
+                rec.load(ch)
+                psi = lambda k, img: float(rec.plans[0].objective(img, rec.p[k], rec.w[k], ch[k].beta,
+                                                                  ch[k].tv_eps).item())
+                out = rec.run(len(ch), [c.beta for c in ch], list(starts), K, **opts)
+                gaps += [(psi(k, out[k]) - pp[k]) / pp[k] for k in range(len(ch))]
+            if details is not None:
+                details[K] = gaps
+            if max(gaps) <= bar:
+                return K
+        return None
+    finally:
+        rec.close()
+
+
 def summarize(results, Ks, tol: float = 1e-3):
     """Per start and K: the median / worst relative objective gap to the plain
     form, (Psi - Psi_plain) / Psi_plain, and the fraction of cases within `tol`."""
@@ -434,7 +416,7 @@ class WarmPipeline:
         pipe.run()                      # enqueue the chain; images in pipe.img
     """
 
-    def __init__(self, geom, n_subsets: int, slices: int, K: int, device, lambda0: float = 0.025,
+    def __init__(self, geom, n_subsets: int, slices: int, K: int, device, lambda0: float = FAST_LAMBDA0,
                  weights: Optional[np.ndarray] = None, cnn_batch: int = 16):
         torch = _torch()
         from . import mvct
@@ -550,22 +532,12 @@ def _train_main(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     log = lambda s: print(s, file=sys.stderr, flush=True)
     t0 = time.perf_counter()
-    hist, tp = [], {}
     init = load_weights(args.init) if args.init else init_params(args.seed)
-    if args.init and args.pair_epochs_skip:
-        cnn = CNN(args.batch, 512, 512, init)
-    else:
-        X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width,
-                              n_iter=args.target_iterations, workers=args.workers, log=log)
-        cnn = CNN(args.batch, X.shape[1], X.shape[2], init)
+    X, Y, tp = make_pairs(range(TRAIN_SEED0, TRAIN_SEED0 + args.pairs), dev, args.width,
+                          n_iter=args.target_iterations, workers=args.workers, log=log)
+    cnn = CNN(args.batch, X.shape[1], X.shape[2], init)
     t1 = time.perf_counter()
-    if not (args.init and args.pair_epochs_skip):
-        hist = train(cnn, X, Y, args.epochs, args.batch, args.lr, args.seed, log, lr_final=args.lr_final)
-        del X, Y
-    psi_hist = []
-    if args.psi_steps > 0:
-        psi_hist = finetune_objective(cnn, range(TRAIN_SEED0, TRAIN_SEED0 + args.psi_cases), dev, args.psi_steps,
-                                      args.batch, args.psi_lr, args.psi_lr_final, args.seed, args.workers, log)
+    hist = train(cnn, X, Y, args.epochs, args.batch, args.lr, args.seed, log, lr_final=args.lr_final)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     params = cnn.params()
@@ -576,8 +548,6 @@ def _train_main(args):
                batch=args.batch, lr=args.lr, lr_final=args.lr_final, seed=args.seed,
                target_iterations=args.target_iterations, target_options="the library defaults",
                init=os.path.basename(args.init) if args.init else None, epoch_loss=hist,
-               objective_finetune=dict(steps=args.psi_steps, lr=args.psi_lr, lr_final=args.psi_lr_final,
-                                       cases=args.psi_cases, mean_psi=psi_hist) if args.psi_steps else None,
                pair_generation_s=t1 - t0, pair_timing=tp, training_s=t2 - t1,
                steps=args.epochs * (args.pairs // args.batch))
     with open(os.path.splitext(args.out)[0] + ".json", "w") as f:
@@ -640,12 +610,6 @@ def _main(argv=None):
         ap.add_argument("--seed", type=int, default=0)
         ap.add_argument("--target-iterations", type=int, default=N_ITER_TARGET)
         ap.add_argument("--init", default=None, help="start from these weights instead of a fresh network")
-        ap.add_argument("--pair-epochs-skip", action="store_true",
-                        help="with --init: no pair training, only the objective fine-tuning")
-        ap.add_argument("--psi-steps", type=int, default=0, help="objective fine-tuning steps after the pairs")
-        ap.add_argument("--psi-lr", type=float, default=1e-4)
-        ap.add_argument("--psi-lr-final", type=float, default=1e-5)
-        ap.add_argument("--psi-cases", type=int, default=1000, help="training cases of the fine-tuning")
         ap.add_argument("--out", default=weights_path())
         return _train_main(ap.parse_args(argv))
     ap.add_argument("--weights", default=None)

@@ -8,7 +8,7 @@ A. The plain form: 512^2 over 40 cm, 800 views x 738 channels, 20 subsets, 500
 B. The batch kernel (the parameter-space persistent launch that the warm-started
    form uses): three slices of the uneven stack's sizes (512^2/800x738,
    384^2/600x552, 256^2/400x368) in one launch, started from their FBP images
-   with lambda0 = 0.025 as the warm chain runs them; each slice against the
+   with the warm chain's lambda0 (0.04); each slice against the
    oracle after 40 sub-iterations, and against a one-slice mvct_recon of 500
    sub-iterations replaying the batch's own lambda sequence.
 
@@ -34,7 +34,7 @@ SEED = 100
 N_ITER = 500
 BETA = 1e-3
 RTOL_IMG = 1e-4
-WARM_LAMBDA0 = 0.025
+WARM_LAMBDA0 = 0.04   # warmstart.FAST_LAMBDA0
 BATCH_GEOMS = (ph.GEOM_512, ph.GEOM_384, ph.GEOM_256)
 BATCH_SEEDS = (50200, 50201, 50202)
 BATCH_ORACLE_ITERS = 40
