@@ -155,7 +155,7 @@ void free_plan(mvct_plan_s *P)
     void *ptrs[] = {P->rays, P->ray_range, P->views, P->a1t, P->a1, P->pad[0], P->pad[1], P->pad[2], P->pad[3],
                     P->pad_ones, P->sino_tmp, P->D, P->e4, P->tile_part, P->back_part, P->tile_flag, P->partials, P->partials2,
                     P->tv_sum, P->bar, P->phase_ns, P->loop_state, P->hist, P->sched,
-                    P->d_slice, P->d_group, P->d_block_group, P->d_count, P->fbp_g, P->fbp_cos, P->fbp_q, P->sorder,
+                    P->d_slice, P->d_group, P->d_block_group, P->d_count, P->sm_slots, P->fbp_g, P->fbp_cos, P->fbp_q, P->sorder,
                     P->pad16[0], P->pad16[1], P->pad16[2], P->pad16[3], P->p16, P->w16, P->bitems};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -230,6 +230,7 @@ extern "C" int mvct_plan_create(const mvct_geometry *g, int32_t n_subsets, mvct_
               cudaMalloc(&P->d_group, sizeof(GroupDesc)) == cudaSuccess &&
               cudaMalloc(&P->d_block_group, sizeof(int) * std::max(1, P->recon_grid)) == cudaSuccess &&
               cudaMalloc(&P->d_count, sizeof(unsigned int) * kGroupSyncWords) == cudaSuccess &&
+              cudaMalloc(&P->sm_slots, sizeof(int) * std::max(1, P->num_sms)) == cudaSuccess &&
               cudaMalloc(&P->sorder, sizeof(int) * std::max(1, n_subsets)) == cudaSuccess &&
               (!balanced || cudaMalloc(&P->bitems, sizeof(int4) * P->recon_grid) == cudaSuccess);
     if (!ok) {

@@ -11,9 +11,9 @@
 //  * fused mean-squared-error loss and Adam.
 // Every reduction has a fixed order: training is deterministic.
 //
-// Layouts: activations [N][H+2][W+2][32] BF16 (NHWC, zero one-pixel border that
-// no kernel writes), the scaled input x and the output-layer gradient
-// [N][H+2][W+2] FP32. Convolution = cross-correlation:
+// Layouts: activations [N][H+2][4][W+2][8] BF16 (per padded row four planes of
+// channel octets, zero one-pixel border that no kernel writes; see aoff), the
+// scaled input x and the output-layer gradient [N][H+2][W+2] FP32. Convolution = cross-correlation:
 // y[p] = sum_{tap} x[p + off(tap)] w[tap], tap = 3 ky + kx, off = (ky-1, kx-1).
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -73,6 +73,25 @@ __device__ __forceinline__ size_t apix(int n, int y, int x, int H, int W)
     return ((size_t)n * (H + 2) + (y + 1)) * (W + 2) + (x + 1);
 }
 
+// 32-channel activations: per padded row, four planes of channel octets,
+// [N][H+2][4][W+2][8] BF16 with a zero one-pixel border. Element offset of octet
+// q (channels 8q .. 8q+7, 16 bytes) of pixel (y, x), y in -1..H, x in -1..W: a
+// warp's 16-byte accesses to consecutive pixels of one octet are contiguous, and
+// the tensor memory accelerator fetches a tile's strip as whole octet rows.
+__device__ __forceinline__ size_t aoff(int n, int y, int x, int q, int H, int W)
+{
+    return (((size_t)n * (H + 2) + (y + 1)) * 4 + q) * (size_t)(W + 2) * 8 + (size_t)(x + 1) * 8;
+}
+
+__device__ __forceinline__ uint4 pack_bf16x8(const float *v)
+{
+    uint4 o;
+    __nv_bfloat162 *b = (__nv_bfloat162 *)&o;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+    return o;
+}
+
 // ---- weight and bias gradient of a 32 -> 32 layer on tensor cores ---------
 // part[block][tap][ci][co] = sum over the block's pixels p of
 //   a[p + off(tap)][ci] * d[p][co]   (a: layer input, d: pre-activation gradient)
@@ -108,7 +127,7 @@ __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ 
             const int ty = px / (TW + 2), tx = px - ty * (TW + 2);
             const int gy = y0 + ty - 1, gx = x0 + tx - 1;
             uint4 v = make_uint4(0, 0, 0, 0);
-            if (gy <= H && gx <= W) v = *((const uint4 *)(a + apix(n, gy, gx, H, W) * CH) + q);
+            if (gy <= H && gx <= W) v = *(const uint4 *)(a + aoff(n, gy, gx, q, H, W));
             *((uint4 *)(s_a + px * SPAD) + q) = v;
         }
         for (int k = tid; k < TH * TW * 4; k += 288) {
@@ -116,7 +135,7 @@ __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ 
             const int ty = px / TW, tx = px - ty * TW;
             const int gy = y0 + ty, gx = x0 + tx;
             uint4 v = make_uint4(0, 0, 0, 0); // outside the image: zero gradient
-            if (gy < H && gx < W) v = *((const uint4 *)(d + apix(n, gy, gx, H, W) * CH) + q);
+            if (gy < H && gx < W) v = *(const uint4 *)(d + aoff(n, gy, gx, q, H, W));
             *((uint4 *)(s_d + px * SPAD) + q) = v;
         }
         __syncthreads();
@@ -207,16 +226,17 @@ __global__ void __launch_bounds__(256) k_conv_in(const float *__restrict__ x, co
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap)
             in[tap] = __ldg(x + apix(n, y + tap / 3 - 1, xx + tap % 3 - 1, H, W));
-        __nv_bfloat16 *o = out + apix(n, y, xx, H, W) * CH;
 #pragma unroll
-        for (int c2 = 0; c2 < CH; c2 += 2) {
-            float v0 = s_w[9 * CH + c2], v1 = s_w[9 * CH + c2 + 1];
+        for (int q = 0; q < 4; ++q) {
+            float v[8];
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                v0 = fmaf(in[tap], s_w[tap * CH + c2], v0);
-                v1 = fmaf(in[tap], s_w[tap * CH + c2 + 1], v1);
+            for (int c = 0; c < 8; ++c) {
+                float t = s_w[9 * CH + 8 * q + c];
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) t = fmaf(in[tap], s_w[tap * CH + 8 * q + c], t);
+                v[c] = fmaxf(t, 0.f);
             }
-            *(__nv_bfloat162 *)(o + c2) = __floats2bfloat162_rn(fmaxf(v0, 0.f), fmaxf(v1, 0.f));
+            *(uint4 *)(out + aoff(n, y, xx, q, H, W)) = pack_bf16x8(v);
         }
     }
 }
@@ -245,10 +265,9 @@ __global__ void __launch_bounds__(256) k_conv_out(const __nv_bfloat16 *__restric
         float acc = bias;
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
-            const uint4 *src = (const uint4 *)(a7 + apix(n, yy + tap / 3 - 1, xx + tap % 3 - 1, H, W) * CH);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint4 v = __ldg(src + q);
+                const uint4 v = __ldg((const uint4 *)(a7 + aoff(n, yy + tap / 3 - 1, xx + tap % 3 - 1, q, H, W)));
                 const __nv_bfloat162 *h = (const __nv_bfloat162 *)&v;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
@@ -294,18 +313,20 @@ __global__ void __launch_bounds__(256) k_conv_out_bwd(const float *__restrict__ 
         float g[9];
 #pragma unroll
         for (int tap = 0; tap < 9; ++tap) g[tap] = __ldg(dout + apix(n, yy - (tap / 3 - 1), xx - (tap % 3 - 1), H, W));
-        const size_t base = apix(n, yy, xx, H, W) * CH;
 #pragma unroll
-        for (int c2 = 0; c2 < CH; c2 += 2) {
-            float v0 = 0.f, v1 = 0.f;
+        for (int q = 0; q < 4; ++q) {
+            const size_t o = aoff(n, yy, xx, q, H, W);
+            const uint4 mv = __ldg((const uint4 *)(a7 + o));
+            const __nv_bfloat16 *m = (const __nv_bfloat16 *)&mv;
+            float v[8];
 #pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-                v0 = fmaf(g[tap], s_w[tap * CH + c2], v0);
-                v1 = fmaf(g[tap], s_w[tap * CH + c2 + 1], v1);
+            for (int c = 0; c < 8; ++c) {
+                float t = 0.f;
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) t = fmaf(g[tap], s_w[tap * CH + 8 * q + c], t);
+                v[c] = __bfloat162float(m[c]) > 0.f ? t : 0.f;
             }
-            const float2 m = __bfloat1622float2(*(const __nv_bfloat162 *)(a7 + base + c2));
-            *(__nv_bfloat162 *)(d7 + base + c2) =
-                __floats2bfloat162_rn(m.x > 0.f ? v0 : 0.f, m.y > 0.f ? v1 : 0.f);
+            *(uint4 *)(d7 + o) = pack_bf16x8(v);
         }
     }
 }
@@ -317,7 +338,7 @@ __global__ void __launch_bounds__(256) k_conv_out_bwd(const float *__restrict__ 
 //   MODE 1 (last layer):  part[b][tap*32 + ci] = sum_p a7[p + off][ci] dout[p],
 //                          part[b][288]        = sum_p dout[p] (289 .. 319 zero)
 // narrow = xs / dout: FP32 padded [N][H+2][W+2]; wide = d1 / a7: BF16 padded
-// NHWC. 320 threads: warp w < 9 owns tap w (lane = channel), warp 9 the bias.
+// octet planes (aoff). 320 threads: warp w < 9 owns tap w (lane = channel), warp 9 the bias.
 // Blocks stride over 8 x 16 output tiles staged in shared memory, the shifted
 // operand with its one-pixel halo.
 constexpr int EDGE_LEN = 9 * CH + CH;
@@ -348,7 +369,7 @@ __global__ void __launch_bounds__(320) k_dw_edge(const float *__restrict__ narro
             const int gy = y0 + ty - o, gx = x0 + tx - o;
             const bool ok = MODE == 1 ? (gy <= H && gx <= W) : (gy < H && gx < W);
             uint4 v = make_uint4(0, 0, 0, 0);
-            if (ok) v = *((const uint4 *)(wide + apix(n, gy, gx, H, W) * CH) + q);
+            if (ok) v = *(const uint4 *)(wide + aoff(n, gy, gx, q, H, W));
             *((uint4 *)(s_w + px * CH) + q) = v;
         }
         for (int px = tid; px < NP; px += 320) {
@@ -534,17 +555,18 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return fn;
 }
 
-// 3D map {32 channels, W + 2 pixels, n (H + 2) rows} of a padded NHWC BF16
-// activation buffer, box {8, 130, 3}: one channel octet of a tile's input strip.
+// 4D map {8 channels, W + 2 pixels, 4 octets, n (H + 2) rows} of a padded
+// octet-plane BF16 activation buffer (aoff), box {8, 130, 4, 3}: a tile's whole
+// input strip, landing in shared memory as [3 rows][4 octets][130 pixels][8].
 int act_map(CUtensorMap *m, const __nv_bfloat16 *base, int n, int H, int W)
 {
     auto enc = tensor_map_encoder();
     if (!enc) return mvct_fail(MVCT_ECUDA, "mvct_cnn: cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[3] = {(cuuint64_t)CH, (cuuint64_t)(W + 2), (cuuint64_t)n * (H + 2)};
-    const cuuint64_t strides[2] = {(cuuint64_t)CH * 2, (cuuint64_t)(W + 2) * CH * 2};
-    const cuuint32_t box[3] = {8, (cuuint32_t)tc::PIX, 3};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)base, dims, strides, box, estr,
+    const cuuint64_t dims[4] = {8, (cuuint64_t)(W + 2), 4, (cuuint64_t)n * (H + 2)};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)(W + 2) * 16, (cuuint64_t)(W + 2) * 64};
+    const cuuint32_t box[4] = {8, (cuuint32_t)tc::PIX, 4, 3};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return mvct_fail(MVCT_ECUDA, "mvct_cnn: cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -655,7 +677,7 @@ extern "C" int mvct_cnn_create(int32_t nmax, int32_t h, int32_t w, double scale,
     alloc((void **)&c->part, sizeof(float) * (size_t)c->part_blocks * MID_SIZE);
     alloc((void **)&c->loss_part, sizeof(double) * c->num_sms * 8);
     alloc((void **)&c->tc_err, sizeof(int));
-    c->tc_grid = c->num_sms * 2; // 2 blocks of 93.8 KB shared memory per SM
+    c->tc_grid = c->num_sms * 2; // 2 blocks of 93.5 KB shared memory per SM
     ok = ok && cudaFuncSetAttribute(tc::k_conv32_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     tc::SMEM_BYTES) == cudaSuccess &&
          cudaFuncSetAttribute(tc::k_conv32_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES) ==

@@ -14,13 +14,12 @@
 // is 8 rows (pixels or output channels) x 16 bytes (8 channels of K) stored
 // contiguously (128 B); core matrices 8 rows further along M/N are SBO = 128 B
 // apart, the next 8 channels along K are LBO bytes apart.
-//   A strip (two stages): [4 channel octets][3 rows][130 pixels][8] BF16, each
-//            octet plane padded to 6,272 B; loaded by the tensor memory
-//            accelerator (cp.async.bulk.tensor, one 8 x 130 x 3 box per octet
-//            from a 3D map of the padded NHWC activations, pixels past the row
-//            end zero-filled) and completed on a per-stage mbarrier. Tap
-//            (ky, kx), K-step kk starts at 2kk*6272 + (ky*130 + kx)*16 B,
-//            LBO = 6272 B (the next octet plane).
+//   A strip (a ring of STAGES): [3 rows][4 channel octets][130 pixels][8]
+//            BF16 (24,960 B), loaded by the tensor memory accelerator
+//            (cp.async.bulk.tensor, one 8 x 130 x 4 x 3 box of a 4D map of the
+//            octet-plane activations, pixels past the row end zero-filled) and
+//            completed on a per-stage mbarrier. Tap (ky, kx), K-step kk starts
+//            at ((ky*4 + 2kk)*130 + kx)*16 B, LBO = 130*16 B (the next octet).
 //   B:       [9 taps][4 input-channel octets][32 co][8] BF16 (18,432 B);
 //            tap, kk starts at (tap*4 + 2kk)*32*16 B, LBO = 32*16 B.
 // Each persistent block loads its layer's weights once and walks tiles
@@ -40,9 +39,9 @@ namespace tc {
 
 constexpr int M = 128;                        // output pixels per tile
 constexpr int PIX = M + 2;                    // strip pixels per row (one halo pixel each side)
-constexpr int PLANE = 6272;                   // one channel octet of the strip: 3 x 130 x 16 B, padded to 128 B
-constexpr int STRIP_TX = 4 * 3 * PIX * 16;    // bytes the four boxes of a strip deliver (24,960)
-constexpr int A_BYTES = 4 * PLANE;            // 25,088 per stage
+constexpr int PLANE = PIX * 16;               // one row of one channel octet of the strip (2,080 B)
+constexpr int STRIP_TX = 3 * 4 * PLANE;       // bytes the strip's box delivers (24,960)
+constexpr int A_BYTES = STRIP_TX;             // per stage (a multiple of 128 B)
 constexpr int STAGES = 3;                     // strips in flight
 constexpr int ACCS = 2;                       // TMEM accumulators (the epilogue of one tile overlaps the next MMAs)
 constexpr int B_BYTES = 9 * 4 * 32 * 16;      // 18,432
@@ -119,12 +118,13 @@ __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// One 3D box of the tensor map at (c0, c1, c2) into shared memory, completing on bar.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *tmap, int c0, int c1, int c2, uint32_t bar)
+// One 4D box of the tensor map at (c0, c1, c2, c3) into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
 {
-    asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                 "%4}], [%5];" ::"r"(dst),
-                 "l"((unsigned long long)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
+                 "%4, %5}], [%6];" ::"r"(dst),
+                 "l"((unsigned long long)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
                  : "memory");
 }
 
@@ -148,9 +148,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 
 // MODE 0 (forward): out = relu(conv(in, wk) + bias).
 // MODE 1 (input gradient): out = conv(in, wk) * [mask > 0].
-// in (through tmap: 3D map {32 channels, W + 2 pixels, N (H + 2) rows} of the
-// padded NHWC BF16 input, box {8, 130, 3}) / mask / out: padded NHWC
-// [N][H+2][W+2][32] BF16; wk: [9][32 n][32 k] BF16.
+// in (through tmap: 4D map {8 channels, W + 2 pixels, 4 octets, N (H + 2) rows}
+// of the input, box {8, 130, 4, 3}) / mask / out: padded octet planes
+// [N][H+2][4][W+2][8] BF16 (aoff); wk: [9][32 n][32 k] BF16.
 // Warp-specialised pipeline over the block's tiles i = 0, 1, ... (tile
 // blockIdx.x + i*gridDim.x): warp 0 fetches strip i into stage i mod STAGES once
 // the MMAs of tile i - STAGES have released it (empty); warp 1 waits for the
@@ -237,8 +237,7 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ C
                 int n, y, x0;
                 tile_at(i, n, y, x0);
                 expect_tx(full_b(s), STRIP_TX);
-                for (int q = 0; q < 4; ++q)
-                    tma_load_3d(sA_a + s * A_BYTES + q * PLANE, &tmap, q * 8, x0, n * (H + 2) + y, full_b(s));
+                tma_load_4d(sA_a + s * A_BYTES, &tmap, 0, x0, 0, n * (H + 2) + y, full_b(s));
             }
         }
     } else if (warp == 1) {
@@ -258,7 +257,7 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ C
                     const int ky = tap / 3, kx = tap - 3 * ky;
 #pragma unroll
                     for (int kk = 0; kk < 2; ++kk) {
-                        const uint64_t ad = smem_desc(a0 + 2 * kk * PLANE + (ky * PIX + kx) * 16, PLANE, 128);
+                        const uint64_t ad = smem_desc(a0 + ((ky * 4 + 2 * kk) * PIX + kx) * 16, PLANE, 128);
                         const uint64_t bd = smem_desc(sB_a + (tap * 4 + 2 * kk) * CH * 16, CH * 16, 128);
                         mma_f16(d, ad, bd, (tap | kk) != 0 ? 1u : 0u);
                     }
@@ -287,28 +286,21 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ C
             tile_at(i, n, y, x0);
             const int x = x0 + quarter * 32 + lane;
             if (x < W) {
-                const size_t base = apix(n, y, x, H, W) * CH;
-                uint4 o[4];
-                __nv_bfloat162 *ob = (__nv_bfloat162 *)o;
-                if (MODE == 0) {
 #pragma unroll
-                    for (int c = 0; c < 16; ++c)
-                        ob[c] = __floats2bfloat162_rn(fmaxf(acc[2 * c] + __ldg(bias + 2 * c), 0.f),
-                                                      fmaxf(acc[2 * c + 1] + __ldg(bias + 2 * c + 1), 0.f));
-                } else {
-                    uint4 mv[4];
+                for (int q = 0; q < 4; ++q) {
+                    const size_t o = aoff(n, y, x, q, H, W);
+                    float v[8];
+                    if (MODE == 0) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) mv[q] = __ldg((const uint4 *)(mask + base) + q);
-                    const __nv_bfloat162 *mb = (const __nv_bfloat162 *)mv;
+                        for (int c = 0; c < 8; ++c) v[c] = fmaxf(acc[8 * q + c] + __ldg(bias + 8 * q + c), 0.f);
+                    } else {
+                        const uint4 mv = __ldg((const uint4 *)(mask + o));
+                        const __nv_bfloat16 *m = (const __nv_bfloat16 *)&mv;
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        const float2 m = __bfloat1622float2(mb[c]);
-                        ob[c] = __floats2bfloat162_rn(m.x > 0.f ? acc[2 * c] : 0.f,
-                                                      m.y > 0.f ? acc[2 * c + 1] : 0.f);
+                        for (int c = 0; c < 8; ++c) v[c] = __bfloat162float(m[c]) > 0.f ? acc[8 * q + c] : 0.f;
                     }
+                    *(uint4 *)(out + o) = pack_bf16x8(v);
                 }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) *((uint4 *)(out + base) + q) = o[q];
             }
         }
     }

@@ -426,7 +426,8 @@ struct Barrier {
     unsigned int pad0[31];
     int err;              // 1: a block gave up waiting (timeout)
     int data_err;         // 1: non-finite / negative input detected in set-up
-    unsigned int pad1[30];
+    int place_err;        // 1: the loop's blocks were not spread over the SMs as its launch assumed
+    unsigned int pad1[29];
 };
 
 __device__ __forceinline__ unsigned long long global_ns()

@@ -88,6 +88,13 @@ struct LoopArgs {
     int debug_unreachable;
     int poisson;              // 1: Poisson data term, e = w - exp(-q)
     int lambda_rule;          // MVCT_LAMBDA_*: which square differences Eq. 4-5 compare
+    // One-slice launches of place_per_sm blocks on each of place_sms SMs (0: off):
+    // a block takes the index slot * place_sms + (its SM), slot = its arrival
+    // order on that SM (counted in sm_slots, zeroed before the launch), so that
+    // index b runs on SM b mod place_sms, as the balanced phase-B plan and the
+    // phase-F ray deal assume (the hardware, not the block index, picks the SM).
+    int *sm_slots;
+    int place_sms, place_per_sm;
 };
 
 // Batches of up to kParamSlices slices pass their descriptors in the kernel
@@ -141,6 +148,7 @@ struct mvct_plan_s {
     mvct::SliceDesc *d_slice = nullptr; // the one-slice launch description
     mvct::GroupDesc *d_group = nullptr;
     int *d_block_group = nullptr;       // [recon_grid] zeros
+    int *sm_slots = nullptr;            // [num_sms] blocks of the loop launch seen on each SM
     unsigned int *d_count = nullptr;    // group barrier counter and PhiPub (kGroupSyncWords words)
     bool in_batch = false;              // owned by a batch (its scratch is in use there)
     // 16-bit storage buffers (allocated on first use): padded ping-pong image

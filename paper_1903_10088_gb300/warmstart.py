@@ -581,6 +581,15 @@ def _evaluate_main(args):
     line = dict(seeds=[seeds[0], seeds[-1]], Ks=args.Ks, warm_opts=warm,
                 weights=os.path.basename(args.weights or weights_path()),
                 summary=summarize(res, args.Ks), host_gen_s=t_gen, gpu_eval_s=t_gpu)
+    if args.bar:
+        # the per-slice bar over all the seeds, from the network's start and from FBP
+        cnn = CNN(16, cases[0].geom.n, cases[0].geom.n, load_weights(args.weights))
+        for name, net in (("cnn", cnn), ("fbp", None)):
+            det = {}
+            k = sub_iterations_to_bar(net, cases, dev, K_GRID, width=args.width, details=det)
+            line[f"bar_{name}"] = dict(K=k, max_gap_by_K={str(kk): float(max(v)) for kk, v in det.items()},
+                                       median_gap_by_K={str(kk): float(np.median(v)) for kk, v in det.items()})
+        cnn.close()
     if args.per_seed:
         line["per_seed"] = res
     print(json.dumps(line))
@@ -618,6 +627,8 @@ def _main(argv=None):
     ap.add_argument("--Ks", type=int, nargs="+", default=[25, 50, 100])
     ap.add_argument("--lambda0", type=float, default=None, help="lambda0 of the network-started runs")
     ap.add_argument("--per-seed", action="store_true")
+    ap.add_argument("--bar", action="store_true", help="also search the smallest K at which every seed is within "
+                                                       "1e-3 of the plain form (network and FBP starts)")
     return _evaluate_main(ap.parse_args(argv))
 
 

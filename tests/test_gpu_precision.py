@@ -17,8 +17,8 @@ pytestmark = pytest.mark.gpu
 
 STORAGES = ("f32", "bf16", "f16")
 # relative L2 bounds against the oracle (lambda replayed). Full size, measured on
-# GB300 after 50 / 100 / 500 sub-iterations: FP32 6.4e-7 / 7.1e-7 / 1.4e-6,
-# FP16 1.7e-4 / 3.0e-4 / 7.0e-4, BF16 1.4e-3 / 2.4e-3 / 5.6e-3.
+# GB300 after 50 / 100 / 500 sub-iterations: FP32 5.1e-7 / 5.1e-7 / 2.4e-6,
+# FP16 8.5e-5 / 1.8e-4 / 1.2e-3, BF16 6.8e-4 / 1.4e-3 / 9.4e-3.
 BOUND_SMALL = {"f32": 1e-4, "bf16": 2e-2, "f16": 3e-3}
 BOUND_FULL = {"f32": 1e-4, "bf16": 1.5e-2, "f16": 2e-3}
 
