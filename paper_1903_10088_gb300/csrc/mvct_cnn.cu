@@ -15,8 +15,6 @@
 // channel octets, zero one-pixel border that no kernel writes; see aoff), the
 // scaled input x and the output-layer gradient [N][H+2][W+2] FP32. Convolution = cross-correlation:
 // y[p] = sum_{tap} x[p + off(tap)] w[tap], tap = 3 ky + kx, off = (ky-1, kx-1).
-#include <cuda.h>
-#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -538,41 +536,6 @@ void free_cnn(mvct_cnn_s *c)
     delete c;
 }
 
-// The driver's tensor-map encoder, looked up once through the runtime.
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
-{
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-        else
-            cudaGetLastError();
-    }
-    return fn;
-}
-
-// 4D map {8 channels, W + 2 pixels, 4 octets, n (H + 2) rows} of a padded
-// octet-plane BF16 activation buffer (aoff), box {8, 130, 4, 3}: a tile's whole
-// input strip, landing in shared memory as [3 rows][4 octets][130 pixels][8].
-int act_map(CUtensorMap *m, const __nv_bfloat16 *base, int n, int H, int W)
-{
-    auto enc = tensor_map_encoder();
-    if (!enc) return mvct_fail(MVCT_ECUDA, "mvct_cnn: cuTensorMapEncodeTiled is not available");
-    const cuuint64_t dims[4] = {8, (cuuint64_t)(W + 2), 4, (cuuint64_t)n * (H + 2)};
-    const cuuint64_t strides[3] = {16, (cuuint64_t)(W + 2) * 16, (cuuint64_t)(W + 2) * 64};
-    const cuuint32_t box[4] = {8, (cuuint32_t)tc::PIX, 4, 3};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return mvct_fail(MVCT_ECUDA, "mvct_cnn: cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return MVCT_OK;
-}
-
 int grid_for(const mvct_cnn_s *c, long long work, int per_block)
 {
     const long long want = (work + per_block - 1) / per_block;
@@ -587,11 +550,8 @@ int cnn_forward(mvct_cnn_s *c, int n, float *out, bool with_target, cudaStream_t
     const long long pix = (long long)n * H * W;
     k_conv_in<<<grid_for(c, pix, 256), 256, 0, st>>>(c->xs, c->wf + OFF_W1, c->wf + OFF_B1, c->act[0], n, H, W);
     for (int l = 0; l < MID; ++l) {
-        CUtensorMap m;
-        const int rc = act_map(&m, c->act[l], n, H, W);
-        if (rc) return rc;
         tc::k_conv32_tc<0><<<c->tc_grid, tc::THREADS, tc::SMEM_BYTES, st>>>(
-            m, c->wk_fwd + (size_t)l * 9 * CH * CH, c->wf + OFF_MID + l * MID_SIZE + 9 * CH * CH, nullptr,
+            c->act[l], c->wk_fwd + (size_t)l * 9 * CH * CH, c->wf + OFF_MID + l * MID_SIZE + 9 * CH * CH, nullptr,
             c->act[l + 1], n, H, W, c->tc_err);
     }
     const int gb = grid_for(c, pix, 256);
@@ -619,11 +579,8 @@ int cnn_backward(mvct_cnn_s *c, int n, cudaStream_t st)
         k_reduce_parts<<<(MID_SIZE + 31) / 32, 256, 0, st>>>(c->part, PB, MID_SIZE, MID_SIZE,
                                                             c->g + OFF_MID + l * MID_SIZE);
         // input gradient, masked by the previous activation (act[l])
-        CUtensorMap m;
-        const int rc = act_map(&m, c->dgrad[cur], n, H, W);
-        if (rc) return rc;
         tc::k_conv32_tc<1><<<c->tc_grid, tc::THREADS, tc::SMEM_BYTES, st>>>(
-            m, c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l], c->dgrad[cur ^ 1], n, H, W, c->tc_err);
+            c->dgrad[cur], c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l], c->dgrad[cur ^ 1], n, H, W, c->tc_err);
         cur ^= 1;
     }
     // first layer: weight and bias gradient (W1 and b1 contiguous) from the scaled input

@@ -15,11 +15,15 @@
 // contiguously (128 B); core matrices 8 rows further along M/N are SBO = 128 B
 // apart, the next 8 channels along K are LBO bytes apart.
 //   A strip (a ring of STAGES): [3 rows][4 channel octets][130 pixels][8]
-//            BF16 (24,960 B), loaded by the tensor memory accelerator
-//            (cp.async.bulk.tensor, one 8 x 130 x 4 x 3 box of a 4D map of the
-//            octet-plane activations, pixels past the row end zero-filled) and
-//            completed on a per-stage mbarrier. Tap (ky, kx), K-step kk starts
-//            at ((ky*4 + 2kk)*130 + kx)*16 B, LBO = 130*16 B (the next octet).
+//            BF16 (24,960 B). Each (row, octet) line of the strip is one
+//            contiguous run of the padded octet-plane activations (130 pixels x
+//            16 B), so the strip arrives as 12 bulk asynchronous copies
+//            (cp.async.bulk, the tensor memory accelerator's untiled form)
+//            completed on a per-stage mbarrier; at a ragged row end the copies
+//            are shortened to the pixels that exist, and the stale rest of the
+//            line only reaches accumulator rows of pixels past the row end,
+//            which are not written. Tap (ky, kx), K-step kk starts at
+//            ((ky*4 + 2kk)*130 + kx)*16 B, LBO = 130*16 B (the next octet).
 //   B:       [9 taps][4 input-channel octets][32 co][8] BF16 (18,432 B);
 //            tap, kk starts at (tap*4 + 2kk)*32*16 B, LBO = 32*16 B.
 // Each persistent block loads its layer's weights once and walks tiles
@@ -29,7 +33,6 @@
 // waits (bounded) for its copy in flight, frees its TMEM and leaves.
 #pragma once
 
-#include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -40,8 +43,7 @@ namespace tc {
 constexpr int M = 128;                        // output pixels per tile
 constexpr int PIX = M + 2;                    // strip pixels per row (one halo pixel each side)
 constexpr int PLANE = PIX * 16;               // one row of one channel octet of the strip (2,080 B)
-constexpr int STRIP_TX = 3 * 4 * PLANE;       // bytes the strip's box delivers (24,960)
-constexpr int A_BYTES = STRIP_TX;             // per stage (a multiple of 128 B)
+constexpr int A_BYTES = 3 * 4 * PLANE;        // one strip per stage (24,960 B, a multiple of 128 B)
 constexpr int STAGES = 3;                     // strips in flight
 constexpr int ACCS = 2;                       // TMEM accumulators (the epilogue of one tile overlaps the next MMAs)
 constexpr int B_BYTES = 9 * 4 * 32 * 16;      // 18,432
@@ -118,13 +120,12 @@ __device__ __forceinline__ void expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// One 4D box of the tensor map at (c0, c1, c2, c3) into shared memory, completing on bar.
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const void *tmap, int c0, int c1, int c2, int c3,
-                                            uint32_t bar)
+// One contiguous run of `bytes` bytes (a multiple of 16, both addresses 16-byte
+// aligned) from global into shared memory, completing on bar.
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
-    asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, "
-                 "%4, %5}], [%6];" ::"r"(dst),
-                 "l"((unsigned long long)tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
 
@@ -148,9 +149,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 
 // MODE 0 (forward): out = relu(conv(in, wk) + bias).
 // MODE 1 (input gradient): out = conv(in, wk) * [mask > 0].
-// in (through tmap: 4D map {8 channels, W + 2 pixels, 4 octets, N (H + 2) rows}
-// of the input, box {8, 130, 4, 3}) / mask / out: padded octet planes
-// [N][H+2][4][W+2][8] BF16 (aoff); wk: [9][32 n][32 k] BF16.
+// in / mask / out: padded octet planes [N][H+2][4][W+2][8] BF16 (aoff);
+// wk: [9][32 n][32 k] BF16.
 // Warp-specialised pipeline over the block's tiles i = 0, 1, ... (tile
 // blockIdx.x + i*gridDim.x): warp 0 fetches strip i into stage i mod STAGES once
 // the MMAs of tile i - STAGES have released it (empty); warp 1 waits for the
@@ -160,7 +160,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 // accumulator (tempty) and write the tile.
 // err: set to 1 if a wait gave up (every role then leaves its loop, bounded).
 template <int MODE>
-__global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__restrict__ in,
                                                        const __nv_bfloat16 *__restrict__ wk,
                                                        const float *__restrict__ bias,
                                                        const __nv_bfloat16 *__restrict__ mask,
@@ -228,7 +228,8 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ C
     if (warp == 0) {
         // copies: the strip of tile i into stage i mod STAGES
         if (lane == 0) {
-            for (int i = 0; i < my_tiles && !*fail; ++i) {
+            int issued = 0;
+            for (int i = 0; i < my_tiles && !*fail; ++i, ++issued) {
                 const int s = i % STAGES;
                 if (i >= STAGES && !wait_bounded(empty_b(s), (uint32_t)(((i / STAGES) + 1) & 1), kLimit)) {
                     give_up();
@@ -236,9 +237,20 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __grid_constant__ C
                 }
                 int n, y, x0;
                 tile_at(i, n, y, x0);
-                expect_tx(full_b(s), STRIP_TX);
-                tma_load_4d(sA_a + s * A_BYTES, &tmap, 0, x0, 0, n * (H + 2) + y, full_b(s));
+                const uint32_t bytes = (uint32_t)min(PIX, W + 2 - x0) * 16u;
+                expect_tx(full_b(s), 12u * bytes);
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        bulk_load(sA_a + s * A_BYTES + (r * 4 + q) * PLANE, in + aoff(n, y - 1 + r, x0 - 1, q, H, W),
+                                  bytes, full_b(s));
             }
+            // after a failure, copies still in flight land before the block's shared
+            // memory is released (a stage's last phase is pending or complete)
+            if (*fail)
+                for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; ++i)
+                    wait_bounded(full_b(i % STAGES), (uint32_t)((i / STAGES) & 1), kLimit);
         }
     } else if (warp == 1) {
         // MMAs of tile i into accumulator i mod ACCS

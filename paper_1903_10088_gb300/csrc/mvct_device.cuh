@@ -172,12 +172,15 @@ __device__ __forceinline__ float joseph_warp(const TS *img, const TS *imgT, int 
 constexpr int kTile = 32;
 constexpr int kAccStride = 33;
 constexpr int kAccFloats = kTile * kAccStride;
+constexpr float kWinMargin = 0.01f; // channels
 
 // Channel window [x, y] of the rays of a view that can carry a non-zero weight to
 // a pixel of the tile whose first row/column are (i_lo, j_lo): a ray with a
 // non-zero Joseph weight passes within one pixel of that pixel's centre, so it
-// crosses the box of pixel centres grown by one pixel; the window is that box's
-// angular extent seen from the source, widened by one channel. Whole warp calls.
+// crosses the box of pixel centres grown by one pixel; the window holds the
+// channels inside that box's angular extent seen from the source, widened by
+// kWinMargin channels against rounding (the FP32 angle is good to ~2e-4
+// channels, a ray's FP32 tap decisions to ~1e-4). Whole warp calls.
 __device__ __forceinline__ int2 tile_window(const Geo &g, float4 vw, int i_lo, int j_lo, int lane)
 {
     const int corner = lane & 3;
@@ -198,8 +201,8 @@ __device__ __forceinline__ int2 tile_window(const Geo &g, float4 vw, int i_lo, i
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    const int c0 = max(0, (int)floorf(fmaxf(lo, -2.f)) - 1);
-    const int c1 = min(g.C - 1, (int)ceilf(fminf(hi, (float)g.C + 1.f)) + 1);
+    const int c0 = max(0, (int)ceilf(fmaxf(lo, -2.f) - kWinMargin));
+    const int c1 = min(g.C - 1, (int)floorf(fminf(hi, (float)g.C + 1.f) + kWinMargin));
     return make_int2(c0, c1);
 }
 
