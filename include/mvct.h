@@ -237,9 +237,11 @@ int mvct_fbp(mvct_plan plan, const float *d_sino, float *d_img, void *stream);
  * The plans (one per slice, all on one device, each in at most one batch) are
  * reconstructed together: the co-resident grid is split into block groups, each
  * group runs the ordered-subset loop of mvct_recon on its own slices with
- * group-local barriers; blocks are given to groups in proportion to each
- * slice's work (views/S x channels x n). A plan in a batch may not be passed to
- * mvct_recon until the batch is destroyed. */
+ * group-local barriers. With at most as many slices as co-resident blocks each
+ * slice is a group of at least one block, and the remaining blocks are dealt one
+ * at a time to the slice with the most work (views/S x channels x n) per block;
+ * with more slices, single-block groups take the slices longest first. A plan in
+ * a batch may not be passed to mvct_recon until the batch is destroyed. */
 typedef struct mvct_batch_s *mvct_batch;
 
 /* Create a batch over `count` distinct plans (host array). Synchronous. */

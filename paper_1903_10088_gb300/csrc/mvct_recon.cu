@@ -26,6 +26,7 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <queue>
 #include <vector>
 
 #include "mvct_plan.h"
@@ -1068,8 +1069,9 @@ extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_bat
         return mvct_fail(MVCT_ELAUNCH, "mvct_batch_create: loop kernel has no occupancy");
     }
 
-    // Partition the grid into groups. Up to G slices: one group per slice, blocks
-    // in proportion to the slice's work (largest remainders, at least one each).
+    // Partition the grid into groups. Up to G slices: one group per slice, at
+    // least one block each, further blocks dealt one at a time to the slice with
+    // the largest work per block.
     // More slices: G one-block groups, slices dealt longest-first to the least
     // loaded group.
     std::vector<double> work(count);
@@ -1077,19 +1079,18 @@ extern "C" int mvct_batch_create(const mvct_plan *plans, int32_t count, mvct_bat
     std::vector<std::vector<int>> members;
     std::vector<int> nblocks;
     if (count <= G) {
-        const double total = std::accumulate(work.begin(), work.end(), 0.0);
+        // highest averages: each further block goes to the slice with the most work
+        // per block, which minimises the largest work per block (the launch ends
+        // with its slowest group)
         nblocks.assign(count, 1);
-        int left = G - count;
-        std::vector<std::pair<double, int>> rem;
-        for (int i = 0; i < count; ++i) {
-            const double ideal = G * work[i] / total - 1.0;
-            const int extra = std::max(0, std::min(left, (int)std::floor(ideal)));
-            nblocks[i] += extra;
-            left -= extra;
-            rem.push_back({ideal - extra, i});
+        std::priority_queue<std::pair<double, int>> pq;
+        for (int i = 0; i < count; ++i) pq.push({work[i], -i});
+        for (int left = G - count; left > 0; --left) {
+            const int i = -pq.top().second;
+            pq.pop();
+            nblocks[i] += 1;
+            pq.push({work[i] / nblocks[i], -i});
         }
-        std::sort(rem.begin(), rem.end(), [](auto &x, auto &y) { return x.first > y.first; });
-        for (int k = 0; left > 0 && k < count; ++k, --left) nblocks[rem[k].second] += 1;
         for (int i = 0; i < count; ++i) members.push_back({i});
     } else {
         std::vector<int> idx(count);
