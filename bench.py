@@ -606,6 +606,7 @@ def _time_chain(args, dev, ws, wst, cases, K, lam0, flush):
         e1.record(cur)
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
+    pipe.check()                                     # the timed and end-to-end runs succeeded
     e2e_t = max_over_ranks(float(np.sum(e2e_ms)), dev)
     psi = np.array([float(pipe.plans[0].objective(IMG[k], P[k], W[k], cases[k].beta, cases[k].tv_eps).item())
                     for k in range(B)])

@@ -302,6 +302,19 @@ int mvct_cnn_get_params(mvct_cnn cnn, float *params);
 /* Inference: d_out[n][h][w] = network(d_in[n][h][w]) (FP32, device). */
 int mvct_cnn_forward(mvct_cnn cnn, const float *d_in, int32_t n, float *d_out, void *stream);
 
+/* Waits of the tensor-core convolutions: each wait on a pipeline barrier gives
+ * up after timeout_ms of GPU time (default 1000; at most 60000), records the
+ * failure and lets the launch finish. debug_stall = 1 is a test knob: the copy
+ * warps issue nothing, so the first wait of every block runs out. Host-side
+ * setting, applies to launches made after the call. */
+int mvct_cnn_set_wait(mvct_cnn cnn, double timeout_ms, int32_t debug_stall);
+
+/* Synchronise the stream and report whether a tensor-core convolution of the
+ * network gave up waiting since the last status call or training step
+ * (MVCT_ETIMEOUT: the outputs of those launches are invalid); clears the flag.
+ * mvct_cnn_forward is asynchronous and graph-capturable and does not check. */
+int mvct_cnn_status(mvct_cnn cnn, void *stream);
+
 /* Mean squared error of the network on (d_in, d_target) in the scaled domain,
  * mean over all n*h*w pixels, written to *loss (host; the call synchronises
  * the stream), and its gradient with respect to the parameters into d_grad

@@ -498,6 +498,8 @@ struct mvct_cnn_s {
     int part_blocks = 0, steps = 0;
     int *tc_err = nullptr;   // set by a tensor-core convolution whose wait gave up
     int tc_grid = 0;         // persistent blocks of the tensor-core convolutions
+    unsigned long long wait_ns = 1000000000ull; // longest mbarrier wait of those convolutions
+    int debug_stall = 0;     // test knob: their copy warps issue nothing
 };
 
 namespace {
@@ -552,7 +554,7 @@ int cnn_forward(mvct_cnn_s *c, int n, float *out, bool with_target, cudaStream_t
     for (int l = 0; l < MID; ++l) {
         tc::k_conv32_tc<0><<<c->tc_grid, tc::THREADS, tc::SMEM_BYTES, st>>>(
             c->act[l], c->wk_fwd + (size_t)l * 9 * CH * CH, c->wf + OFF_MID + l * MID_SIZE + 9 * CH * CH, nullptr,
-            c->act[l + 1], n, H, W, c->tc_err);
+            c->act[l + 1], n, H, W, c->tc_err, c->wait_ns, c->debug_stall);
     }
     const int gb = grid_for(c, pix, 256);
     k_conv_out<<<gb, 256, 0, st>>>(c->act[6], c->wf + OFF_W8, c->wf + OFF_B8, c->xs, with_target ? c->ys : nullptr, out,
@@ -580,7 +582,8 @@ int cnn_backward(mvct_cnn_s *c, int n, cudaStream_t st)
                                                             c->g + OFF_MID + l * MID_SIZE);
         // input gradient, masked by the previous activation (act[l])
         tc::k_conv32_tc<1><<<c->tc_grid, tc::THREADS, tc::SMEM_BYTES, st>>>(
-            c->dgrad[cur], c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l], c->dgrad[cur ^ 1], n, H, W, c->tc_err);
+            c->dgrad[cur], c->wk_bwd + (size_t)l * 9 * CH * CH, nullptr, c->act[l], c->dgrad[cur ^ 1], n, H, W, c->tc_err,
+            c->wait_ns, c->debug_stall);
         cur ^= 1;
     }
     // first layer: weight and bias gradient (W1 and b1 contiguous) from the scaled input
@@ -681,6 +684,35 @@ extern "C" int mvct_cnn_get_params(mvct_cnn c, float *params_out)
     if (!c || !params_out) return mvct_fail(MVCT_EINVAL, "mvct_cnn_get_params: null argument");
     Dev d(c->device);
     CKC(cudaMemcpy(params_out, c->w, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost));
+    return MVCT_OK;
+}
+
+extern "C" int mvct_cnn_set_wait(mvct_cnn c, double timeout_ms, int32_t debug_stall)
+{
+    if (!c) return mvct_fail(MVCT_EINVAL, "mvct_cnn_set_wait: null network");
+    if (!(timeout_ms > 0) || timeout_ms > 60000.0)
+        return mvct_fail(MVCT_EINVAL, "mvct_cnn_set_wait: timeout_ms must be in (0, 60000]");
+    if (debug_stall != 0 && debug_stall != 1) return mvct_fail(MVCT_EINVAL, "mvct_cnn_set_wait: debug_stall must be 0 or 1");
+    c->wait_ns = (unsigned long long)(timeout_ms * 1e6);
+    c->debug_stall = debug_stall;
+    return MVCT_OK;
+}
+
+extern "C" int mvct_cnn_status(mvct_cnn c, void *stream)
+{
+    if (!c) return mvct_fail(MVCT_EINVAL, "mvct_cnn_status: null network");
+    int rc = mvct_check_ptrs(c->device, stream, "mvct_cnn_status", {});
+    if (rc) return rc;
+    Dev d(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int terr = 0;
+    CKC(cudaMemcpyAsync(&terr, c->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKC(cudaStreamSynchronize(st));
+    if (terr) {
+        CKC(cudaMemsetAsync(c->tc_err, 0, sizeof(int), st));
+        CKC(cudaStreamSynchronize(st));
+        return mvct_fail(MVCT_ETIMEOUT, "mvct_cnn: a tensor-core convolution gave up waiting (its output is invalid)");
+    }
     return MVCT_OK;
 }
 

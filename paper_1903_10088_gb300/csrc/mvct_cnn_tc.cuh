@@ -158,14 +158,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
 // 18 MMAs and commits them to empty and tfull; warps 2-5 wait for tfull, read
 // their TMEM lane quarter (warp w reads lanes 32 (w mod 4) ..), release the
 // accumulator (tempty) and write the tile.
-// err: set to 1 if a wait gave up (every role then leaves its loop, bounded).
+// err: set to 1 if a wait gave up (every role then leaves its loop, bounded);
+// kLimit: the longest wait on one mbarrier phase, in ns of global time.
+// stall (test knob): the copy warp issues nothing.
 template <int MODE>
 __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__restrict__ in,
                                                        const __nv_bfloat16 *__restrict__ wk,
                                                        const float *__restrict__ bias,
                                                        const __nv_bfloat16 *__restrict__ mask,
                                                        __nv_bfloat16 *__restrict__ out, int N, int H, int W,
-                                                       int *__restrict__ err)
+                                                       int *__restrict__ err, unsigned long long kLimit,
+                                                       int stall)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *sB = smem + B_OFF;
@@ -178,7 +181,6 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__re
     auto empty_b = [bar0](int s) { return bar0 + 8u * (uint32_t)(STAGES + s); };
     auto tfull_b = [bar0](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + a); };
     auto tempty_b = [bar0](int a) { return bar0 + 8u * (uint32_t)(2 * STAGES + ACCS + a); };
-    constexpr unsigned long long kLimit = 1000000000ull; // 1 s of global time per wait
 
     // weights [tap][co][ci] -> [tap][ci octet][co][8 ci]
     for (int k = tid; k < 9 * CH * 4; k += THREADS) {
@@ -226,8 +228,9 @@ __global__ void __launch_bounds__(THREADS) k_conv32_tc(const __nv_bfloat16 *__re
     };
 
     if (warp == 0) {
-        // copies: the strip of tile i into stage i mod STAGES
-        if (lane == 0) {
+        // copies: the strip of tile i into stage i mod STAGES (none with the stall
+        // test knob: the MMA warp's first wait then runs out)
+        if (lane == 0 && !stall) {
             int issued = 0;
             for (int i = 0; i < my_tiles && !*fail; ++i, ++issued) {
                 const int s = i % STAGES;

@@ -127,7 +127,7 @@ EXPORTS = ["mvct_recon_opts_init", "mvct_plan_create", "mvct_plan_destroy", "mvc
            "mvct_back", "mvct_tv_grad", "mvct_objective", "mvct_objective_grad", "mvct_recon", "mvct_last_error",
            "mvct_tv_grad_noalloc", "mvct_batch_create", "mvct_batch_destroy", "mvct_batch_bind",
            "mvct_batch_run", "mvct_batch_stats", "mvct_fbp", "mvct_cnn_param_count", "mvct_cnn_create",
-           "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step", "mvct_plan_tune", "mvct_batch_tune",
+           "mvct_cnn_destroy", "mvct_cnn_get_params", "mvct_cnn_set_wait", "mvct_cnn_status", "mvct_cnn_forward", "mvct_cnn_grad", "mvct_cnn_train_step", "mvct_plan_tune", "mvct_batch_tune",
            "mvct_plan_set_shape", "mvct_phase_b_plan"]
 
 
@@ -158,6 +158,8 @@ def load_library(path: str = _LIB_PATH) -> ctypes.CDLL:
     lib.mvct_cnn_destroy.argtypes = [vp]
     lib.mvct_cnn_destroy.restype = None
     lib.mvct_cnn_get_params.argtypes = [vp, fp]
+    lib.mvct_cnn_set_wait.argtypes = [vp, ctypes.c_double, i32]
+    lib.mvct_cnn_status.argtypes = [vp, vp]
     lib.mvct_cnn_forward.argtypes = [vp, vp, i32, vp, vp]
     lib.mvct_cnn_grad.argtypes = [vp, vp, vp, i32, vp, dp, vp]
     lib.mvct_cnn_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_double, dp, vp]

@@ -72,6 +72,16 @@ class CNN:
         self._m._check(self._m.lib().mvct_cnn_get_params(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
         return out
 
+    def set_wait(self, timeout_ms: float = 1000.0, debug_stall: bool = False):
+        """``mvct_cnn_set_wait``: wait limit of the tensor-core convolutions (and the
+        stall test knob)."""
+        self._m._check(self._m.lib().mvct_cnn_set_wait(self._h, float(timeout_ms), int(bool(debug_stall))))
+
+    def status(self, stream=None):
+        """``mvct_cnn_status``: raises MvctError (MVCT_ETIMEOUT) if a convolution gave
+        up waiting since the last check."""
+        self._m._check(self._m.lib().mvct_cnn_status(self._h, ctypes.c_void_p(self._m._stream(stream))))
+
     def forward(self, x, out=None, stream=None):
         import torch
 
@@ -472,7 +482,7 @@ class WarmPipeline:
         st.wait_stream(torch.cuda.current_stream(self.device))
         self._chain(st)
         torch.cuda.synchronize(self.device)
-        self.batch.stats(0)                       # raises if the run failed
+        self.check()                              # raises if the run failed
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(st):
             with torch.cuda.graph(g, stream=st):
@@ -498,7 +508,9 @@ class WarmPipeline:
                 "setup_and_loop": marks[2].elapsed_time(marks[3]) / self.B}
 
     def check(self):
-        """Raise if the last run failed (data check or barrier timeout)."""
+        """Raise if a run since the last check failed (the network's convolution
+        waits; the loop's data check or barrier timeout)."""
+        self.cnn.status()
         self.batch.stats(0)
 
     def close(self):

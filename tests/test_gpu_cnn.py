@@ -94,3 +94,37 @@ def test_adam_steps_lower_the_loss(mvct):
     losses = [net.train_step(xs, ys, 1e-3) for _ in range(30)]
     assert losses[-1] < 0.7 * losses[0]
     net.close()
+
+
+def test_convolution_wait_timeout_is_reported(mvct):
+    """Failure path of the tensor-core convolutions without a GPU fault: with the
+    stall knob their copy warps issue nothing, every block's first pipeline wait
+    runs out after the 50 ms limit, the launch finishes, and the host reads
+    MVCT_ETIMEOUT (forward: from the status call; training: from the step). The
+    context stays usable: with the knob off the next forward matches a network
+    that never stalled, bit for bit."""
+    n, h, w = 2, 40, 150
+    x = torch.from_numpy(data((n, h, w), 7)).cuda()
+    p = params_for_test(3)
+    ref_net = ws.CNN(n, h, w, p)
+    ref = ref_net.forward(x)
+    ref_net.status()
+    net = ws.CNN(n, h, w, p)
+    try:
+        net.set_wait(50.0, debug_stall=True)
+        net.forward(x)
+        with pytest.raises(mvct.MvctError) as ei:
+            net.status()
+        assert ei.value.code == -5
+        with pytest.raises(mvct.MvctError) as ei:
+            net.train_step(x, 0.9 * x, 1e-5)
+        assert ei.value.code == -5
+        net.set_wait(1000.0, debug_stall=False)
+        out = net.forward(x)
+        net.status()
+        assert torch.equal(out, ref)
+        with pytest.raises(mvct.MvctError):
+            net.set_wait(0.0)
+    finally:
+        net.close()
+        ref_net.close()
