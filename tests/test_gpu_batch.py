@@ -179,3 +179,35 @@ def test_large_batch_descriptor_array_path(mvct):
         with mvct.Plan(c.geom, c.n_subsets) as plan:
             single, _ = plan.recon(cuda(c.p), cuda(c.w), c.beta, 6)
         assert rel(got[k].cpu().numpy(), single.cpu().numpy()) < 1e-5
+
+
+def highest_averages(work, G):
+    """Blocks per slice: one each, then each further block to the slice with the
+    largest work per block (ties to the lower index)."""
+    blocks = [1] * len(work)
+    for _ in range(G - len(work)):
+        k = max(range(len(work)), key=lambda i: (work[i] / blocks[i], -i))
+        blocks[k] += 1
+    return blocks
+
+
+def test_blocks_dealt_by_work_per_block(mvct):
+    """The grid is split among the slices of an uneven batch so that the largest
+    work per block (views/S x channels x n per block) is as small as it can be:
+    the launch lasts as long as its slowest group. Checked against the
+    highest-averages split computed here, and the two properties that define it."""
+    cases = make_cases(2)
+    _, stats = run_batch(mvct, cases, 2)
+    blocks = [s.grid_blocks for s in stats]
+    G = sum(blocks)
+    work = [c.geom.n_views // c.n_subsets * c.geom.n_channels * c.geom.n for c in cases]
+    assert blocks == highest_averages(work, G)
+    worst = max(w / b for w, b in zip(work, blocks))
+    # taking a block from any slice and giving it to another never lowers the worst ratio
+    for i in range(len(work)):
+        for j in range(len(work)):
+            if i != j and blocks[i] > 1:
+                alt = list(blocks)
+                alt[i] -= 1
+                alt[j] += 1
+                assert max(w / b for w, b in zip(work, alt)) >= worst

@@ -104,7 +104,7 @@ def test_convolution_wait_timeout_is_reported(mvct):
     context stays usable: with the knob off the next forward matches a network
     that never stalled, bit for bit."""
     n, h, w = 2, 40, 150
-    x = torch.from_numpy(data((n, h, w), 7)).cuda()
+    x = torch.from_numpy(data((n, h, w), 7)[0]).cuda()
     p = params_for_test(3)
     ref_net = ws.CNN(n, h, w, p)
     ref = ref_net.forward(x)
