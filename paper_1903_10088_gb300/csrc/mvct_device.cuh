@@ -164,13 +164,16 @@ __device__ __forceinline__ float joseph_warp(const TS *img, const TS *imgT, int 
 // column (or row) of a warp-private accumulator tile, in channel order, so the
 // result is deterministic without atomics.
 //
-// Accumulator layout: 32 rows x 33 floats. Rays whose slope (dy/dx for x-driven,
-// dx/dy for y-driven) is >= 0 use column index j, rays with negative slopes use
-// the mirrored column 31 - j; either way the 32 lanes of a step fall in at least
-// 16 distinct banks.
+// Accumulator layout: 32 x 32 floats per warp, row-major for the warps that take
+// the views whose central ray is x-driven and column-major for the warps that
+// take the y-driven ones. A ray of the warp's own type then touches element
+// lane + 32 a (bank = lane) for any slope: no bank conflicts; rays of the other
+// type (views within the fan's half-angle of 45 degrees) touch 32 lane + a, whose
+// rows a spread over the banks at slopes near +-1. The block sum transposes the
+// column-major part through a padded 32 x 33 scratch tile.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 32;
-constexpr int kAccStride = 33;
+constexpr int kAccStride = 33; // row pitch of the padded scratch tile
 constexpr int kAccFloats = kTile * kAccStride;
 constexpr float kWinMargin = 0.01f; // channels
 
@@ -239,35 +242,29 @@ __device__ __forceinline__ void smem_add(unsigned addr, float v)
 // pj = j_lo + lane - pc, pi = i_lo + lane - pc. Per batch of 32 staged rays a
 // warp vote picks a loop without the per-ray type test when all of them are
 // x-driven (or all y-driven), the usual case away from the 45-degree directions.
-template <bool MIRROR, class Stage>
+template <bool TRANS, class Stage>
 __device__ __forceinline__ void splat_channels(float *acc, float4 *stage, const Stage &load, int c0,
                                                int c1, float pj, float pi, int i_lo, int j_lo, int lane)
 {
     const unsigned acc0 = smem_addr(acc);
-    // x-driven rays: this lane's column; y-driven rays: this lane's row
-    const unsigned col_x = acc0 + 4u * (unsigned)(MIRROR ? (kTile - 1) - lane : lane);
-    const unsigned row_y = acc0 + 4u * (unsigned)(lane * kAccStride);
+    // element (row r, col c) of the tile: r*32 + c (TRANS = false) or c*32 + r
+    const unsigned lane_major = acc0 + 4u * (unsigned)lane;   // + 128 a: bank = lane
+    const unsigned lane_minor = acc0 + 128u * (unsigned)lane; // + 4 a
     auto x_step = [&](const float4 &r) { // x-driven: this lane's column, rows a and a+1
         float f;
         const int a = floor_frac(fmaf(r.y, pj, r.x), f) - i_lo;
         const float w1 = f * r.z, w0 = r.z - w1;
-        const unsigned ad = col_x + 4u * (unsigned)(a * kAccStride);
+        const unsigned ad = TRANS ? lane_minor + 4u * (unsigned)a : lane_major + 128u * (unsigned)a;
         if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
-        if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u * kAccStride, w1);
+        if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + (TRANS ? 4u : 128u), w1);
     };
     auto y_step = [&](const float4 &r) { // y-driven: this lane's row, columns a and a+1
         float f;
         const int a = floor_frac(fmaf(r.y, pi, r.x), f) - j_lo;
         const float w1 = f * r.z, w0 = r.z - w1;
-        if (MIRROR) {
-            const unsigned ad = row_y + 4u * (unsigned)((kTile - 1) - a);
-            if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
-            if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad - 4u, w1);
-        } else {
-            const unsigned ad = row_y + 4u * (unsigned)a;
-            if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
-            if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + 4u, w1);
-        }
+        const unsigned ad = TRANS ? lane_major + 128u * (unsigned)a : lane_minor + 4u * (unsigned)a;
+        if ((unsigned)a < (unsigned)kTile) smem_add(ad, w0);
+        if ((unsigned)(a + 1) < (unsigned)kTile) smem_add(ad + (TRANS ? 128u : 4u), w1);
     };
     for (int cb = c0; cb <= c1; cb += 32) {
         const int c = cb + lane;
@@ -303,13 +300,13 @@ constexpr int kWinBatch = 64;
 
 // One block splats subset rows onto the 32x32 tile (i_lo, j_lo): the rows
 // k = order[j] (or k = j without an order) for j = ja, ja + jstep, ... (< jb).
-// Views whose ray slopes are >= 0 go to warps [0, wpos), the others to warps
-// [wpos, nw) (mirrored accumulator layout), wpos = nw/2. Per batch of up to
-// kWinBatch views, the warps first compute the views' channel windows into
+// Views whose central ray is x-driven go to warps [0, wpos) (row-major
+// accumulators), the others to warps [wpos, nw) (column-major), wpos = nw/2.
+// Per batch of up to kWinBatch views, the warps first compute the views' channel windows into
 // s_win; then the channels of each class, concatenated in view order, are cut
 // into equal contiguous runs, one per warp of the class (a run may span several
-// views or part of one). Returns wpos; after the closing block barrier the tile
-// sum of pixel idx is tile_sum(s_acc, idx, nw, wpos).
+// views or part of one). Returns wpos; after the closing block barrier tile_sums
+// gives the tile.
 template <class MakeStage>
 __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restrict__ views, int subset,
                                            int ja, int jb, int jstep, const int *__restrict__ order,
@@ -319,9 +316,9 @@ __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restric
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nw = blockDim.x >> 5;
     const int wpos = nw / 2;
-    const bool mirror = warp >= wpos;
-    const int nmine = mirror ? nw - wpos : wpos;
-    const int q = mirror ? warp - wpos : warp;
+    const bool trans = warp >= wpos;
+    const int nmine = trans ? nw - wpos : wpos;
+    const int q = trans ? warp - wpos : warp;
     float *acc = s_acc[warp];
     float4 *stage = s_stage[warp];
     const float pj = (float)(j_lo + lane) - g.pc, pi = (float)(i_lo + lane) - g.pc;
@@ -330,14 +327,14 @@ __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restric
     const int nviews = jb > ja ? (jb - ja + jstep - 1) / jstep : 0;
     for (int base = 0; base < nviews; base += kWinBatch) {
         const int cnt = min(kWinBatch, nviews - base);
-        // windows: (c0, c1, mirror class, v) of view `idx` of the batch
+        // windows: (c0, c1, layout class, v) of view `idx` of the batch
         for (int idx = warp; idx < cnt; idx += nw) {
             const int j = ja + (base + idx) * jstep;
             const int k = order ? __ldg(order + j) : j;
             const int v = subset < 0 ? k : subset + k * g.S;
             const float4 vw = __ldg(&views[v]);
             const int2 win = tile_window(g, vw, i_lo, j_lo, lane);
-            if (lane == 0) s_win[idx] = make_int4(win.x, win.y, (vw.z * vw.w < 0.f) ? 1 : 0, k);
+            if (lane == 0) s_win[idx] = make_int4(win.x, win.y, (fabsf(vw.z) < fabsf(vw.w)) ? 1 : 0, k);
         }
         __syncthreads();
         // this class's channel counts of entries lane and lane + 32, exclusive prefix sums
@@ -348,7 +345,7 @@ __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restric
             len[h] = 0;
             if (idx < cnt) {
                 const int4 w = s_win[idx];
-                if ((w.z != 0) == mirror) len[h] = max(0, w.y - w.x + 1);
+                if ((w.z != 0) == trans) len[h] = max(0, w.y - w.x + 1);
             }
             int x = len[h];
 #pragma unroll
@@ -373,7 +370,7 @@ __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restric
             const int k = w.w;
             const int v = subset < 0 ? k : subset + k * g.S;
             const auto st = make_stage(k, v);
-            if (mirror) splat_channels<true>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
+            if (trans) splat_channels<true>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
             else splat_channels<false>(acc, stage, st, c0, c1, pj, pi, i_lo, j_lo, lane);
         }
         __syncthreads(); // s_win is rewritten by the next batch
@@ -382,13 +379,35 @@ __device__ __forceinline__ int splat_views(const Geo &g, const float4 *__restric
     return wpos;
 }
 
-// Block sum of tile pixel idx = ii*32 + jj (see splat_views), warps in order.
-__device__ __forceinline__ float tile_sum(float (*s_acc)[kAccFloats], int idx, int nw, int wpos)
+// Block sums of the tile (after splat_views): v[u] = pixel idx = threadIdx.x + u*256,
+// (ii, jj) = (idx / 32, idx % 32): the row-major accumulators of warps [0, wpos)
+// in warp order, plus the column-major ones of warps [wpos, nw) in warp order,
+// transposed through s_acc[0] (padded rows of 33). Whole block; s_acc is
+// overwritten. Requires 4 * blockDim.x == 1024.
+__device__ __forceinline__ void tile_sums(float (*s_acc)[kAccFloats], int nw, int wpos, float v[4])
 {
-    const int ii = idx >> 5, jj = idx & 31;
-    float v = 0.f;
-    for (int w = 0; w < nw; ++w) v += s_acc[w][ii * kAccStride + (w >= wpos ? (kTile - 1) - jj : jj)];
-    return v;
+    float vt[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int idx = threadIdx.x + u * blockDim.x;
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < wpos; ++w) a += s_acc[w][idx];
+        for (int w = wpos; w < nw; ++w) b += s_acc[w][idx];
+        v[u] = a;
+        vt[u] = b; // column-major element idx: pixel (idx % 32, idx / 32)
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int idx = threadIdx.x + u * blockDim.x;
+        s_acc[0][(idx >> 5) * kAccStride + (idx & 31)] = vt[u];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int idx = threadIdx.x + u * blockDim.x;
+        v[u] += s_acc[0][(idx & 31) * kAccStride + (idx >> 5)];
+    }
 }
 
 // d/dmu[i][j] of TV_eps = sum sqrt(dx^2 + dy^2 + eps) with forward differences

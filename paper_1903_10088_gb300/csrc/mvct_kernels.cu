@@ -123,10 +123,12 @@ k_back_splat(Geo g, const float4 *__restrict__ rays, const float4 *__restrict__ 
                                  [rays, sino, C](int k, int v) {
                                      return StageSino{rays + (size_t)v * C, sino + (size_t)k * C};
                                  });
+    float vals[4];
+    tile_sums(s_acc, kWarps, wpos, vals);
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int idx = threadIdx.x + u * kThreads;
-        const float val = tile_sum(s_acc, idx, kWarps, wpos);
+        const float val = vals[u];
         if (H == 1) {
             const int i = i_lo + (idx >> 5), j = j_lo + (idx & 31);
             if (i < g.n && j < g.n) img[(size_t)i * g.n + j] = val;

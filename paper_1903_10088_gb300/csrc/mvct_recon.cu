@@ -342,8 +342,7 @@ __device__ __forceinline__ bool run_slice(const SD &sd, const GD &grp, const Loo
             const int wpos = splat_views(g, sd.views, s, h, g.Vs, Ht, nullptr, i_lo, j_lo, sh.acc, sh.stage, sh.win,
                                          [e4, C](int k, int) { return StageE4{e4 + (size_t)k * C}; });
             float part_val[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) part_val[u] = tile_sum(sh.acc, threadIdx.x + u * kThreads, kWarps, wpos);
+            tile_sums(sh.acc, kWarps, wpos, part_val);
 
             if (!owner) {
                 const size_t slot = (size_t)slot0 + h;
