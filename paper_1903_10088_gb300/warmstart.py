@@ -571,7 +571,7 @@ def _train_main(args):
 def _evaluate_main(args):
     """Held-out evaluation on the GPU: per seed the plain form (FBP start, 500
     sub-iterations) against network start + K and FBP start + K sub-iterations,
-    judged by the objective Psi (mvct_objective, FP64 reduction; pinned against
+    compared by the objective Psi (mvct_objective, FP64 reduction; pinned against
     the FP64 oracle by the tests); one JSON line: the summary per start and K
     and, with --per-seed, every seed's values."""
     import json
