@@ -29,7 +29,7 @@ namespace cnn {
 constexpr int CH = 32;              // hidden channels
 constexpr int MID = 6;              // 32 -> 32 layers (2..7)
 constexpr int SPAD = 40;            // smem row stride (bf16) of a pixel / kernel row: 80 B, conflict-free ldmatrix
-constexpr int TH = 8, TW = 16;      // output tile of the tensor-core kernels (one warp per tile row)
+constexpr int TH = 8, TW = 16;      // pixel tile of the weight-gradient kernel k_dw32 (one warp per tile row)
 
 // Parameter vector (FP32): W1[9][32], b1[32], {W_l[9][32 ci][32 co], b_l[32]} x 6, W8[9][32], b8[1]
 constexpr int OFF_W1 = 0;
@@ -95,7 +95,7 @@ __device__ __forceinline__ uint4 pack_bf16x8(const float *v)
 //   a[p + off(tap)][ci] * d[p][co]   (a: layer input, d: pre-activation gradient)
 // part[block][9*32*32 + co] = sum over the block's pixels of d[p][co]
 // (the row stride of part is MID_SIZE, the layer's slice of the parameter vector).
-// One warp per tap (9 warps) on the tensor cores; warps 0-7 also sum the bias
+// One warp per tap (9 warps) on mma.sync tensor-core tiles; warps 0-7 also sum the bias
 // gradient, one tile row each. Blocks stride over the output tiles.
 __global__ void __launch_bounds__(288) k_dw32(const __nv_bfloat16 *__restrict__ a,
                                               const __nv_bfloat16 *__restrict__ d, float *__restrict__ part,
