@@ -515,6 +515,12 @@ def run_ours(args):
         "setup_and_loop_ms_per_slice": float(np.mean(step_ms)),
         "loop_phase_ms_per_slice": {"reprojection+residual": float(np.mean(fwd_ms)),
                                     "estimation+tv+update": float(np.mean(back_ms))},
+        # each phase against its half of the tap bytes (the taps the projector reads
+        # equal the residual reads of the matched backprojection); phase times include
+        # the phase's closing group barrier
+        "phase_tap_fraction": {
+            "reprojection": 4 * taps_per_launch / (float(np.mean(fwd_ms)) / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "backprojection": 4 * taps_per_launch / (float(np.mean(back_ms)) / 1e3) / 1e9 / peaks["hbm_gbs"]},
         "roofline": roofline,
         "operator_roofline": dict(operators, bytes="4 B x in-image Joseph taps of the call (taps read by the "
                                                    "projector = residual reads of the matched backprojection)",
