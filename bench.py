@@ -725,8 +725,10 @@ def batched_leg(args, dev, ws, steps, warmup):
     from paper_1903_10088_gb300 import mvct
 
     _, rank, local = dist_env()
-    cases = batch_cases(seed0=1000 + 96 * rank, workers=min(16, os.cpu_count() or 1))
-    n_iter = cases[0].n_iter
+    stack = getattr(args, "stack_slices", 0) or 0
+    groups = [(stack, ph.GEOM_512)] if stack > 0 else ph.BATCH_GROUPS
+    cases = batch_cases(seed0=1000 + 96 * rank, groups=groups, workers=min(16, os.cpu_count() or 1))
+    n_iter = getattr(args, "stack_iters", 0) or cases[0].n_iter
     plans = [mvct.Plan(c.geom, c.n_subsets) for c in cases]
     p = [torch.from_numpy(c.p).to(dev) for c in cases]
     w = [torch.from_numpy(c.w).to(dev) for c in cases]
@@ -796,7 +798,10 @@ def batched_leg(args, dev, ws, steps, warmup):
     achieved = 2 * 4 * tap_total / t_step / 1e9
     out = {
         "value": value, "unit": "slices/s", "ms_per_step": t_max / steps, "steps": steps, "warmup": warmup,
-        "config": dict(BATCH_WORKLOAD, l2="flushed between timed steps (512 MiB write)",
+        "config": dict(BATCH_WORKLOAD if stack <= 0 else
+                       dict(BATCH_WORKLOAD, workload=f"batched stack of {stack} 512^2 slices (a smaller case)",
+                            slices=f"{stack} x 512^2 (800 views x 738 ch)", sub_iterations=n_iter),
+                       l2="flushed between timed steps (512 MiB write)",
                        launch_shape={"view_groups_per_tile": tune["groups"] or "default rule",
                                      "autotuned_ms_per_iter": tune["ms_per_iter"],
                                      "default_ms_per_iter": tune["default_ms_per_iter"]}),
@@ -970,6 +975,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-warm", action="store_true", help="skip the warm-started batched form")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched uneven stack")
+    ap.add_argument("--stack-slices", type=int, default=0,
+                    help="--workload batched: a stack of this many 512^2 slices instead of the uneven stack")
+    ap.add_argument("--stack-iters", type=int, default=0,
+                    help="--workload batched: sub-iterations per step instead of 500")
     ap.add_argument("--ref-threads", type=int, default=0,
                     help="oracle threads for the whole-slice CPU timing (0: every host core)")
     ap.add_argument("--workload", choices=["plain", "batched", "subsets", "ops"], default="plain")
