@@ -842,7 +842,8 @@ def run_batched(args):
 
     mvct.lib()
     leg = batched_leg(args, dev, ws, args.steps, args.warmup)
-    line = dict({"metric": "slices/s of the batched uneven stack at 500 OS-TV iters (plain start)",
+    line = dict({"metric": f"slices/s of the batched stack at {leg['config']['sub_iterations']} OS-TV iters "
+                           "(plain start)",
                  "n_gpus": ws, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                  "dtype": "f32", "data": "synthetic", "gpu_launches": leg["gpu_launches_per_step"] * args.steps},
                 **leg)
